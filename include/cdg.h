@@ -1,0 +1,184 @@
+/*
+ * cdg.h -- C ABI of the GB300 agglomeration h-multigrid solver for Compact
+ * Discontinuous Galerkin (CDG) discretisations of Poisson's equation
+ * (Pan & Persson, "Agglomeration-Based Geometric Multigrid Solvers for Compact
+ * Discontinuous Galerkin Discretizations on Unstructured Meshes").
+ *
+ * Problem (Section 2.1, eq. poisson, sign as in the symmetric positive definite
+ * form): -div(kappa grad u) = f in Omega, u = g_D on Gamma_D, kappa du/dn = g_N
+ * on Gamma_N, |Gamma_D| > 0, kappa = 1 unless given.  Discretisation: CDG with
+ * switch function S (Section 2.2) and penalty C_D = gamma / h_avg, primal form
+ * A u = b (Section 2.3, eq. primal_form).  Solver: CG preconditioned by one
+ * V(nu_pre, nu_post) cycle of damped block Jacobi (alpha = omega, Section 4.3)
+ * over the greedy agglomeration hierarchy (Section 3.2, Algorithm 2) with
+ * flux-coarsened operators (Section 4.1).
+ *
+ * Conventions
+ *  - Every function returns CDG_OK (0) or one of the error codes below; the
+ *    message of the last failure of a handle is cdg_last_error(handle), that of
+ *    a failed cdg_create is cdg_last_error(NULL) (per thread).
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *    A handle owns its host-side hierarchy; its device data lives inside ONE
+ *    caller-allocated device buffer given to cdg_bind_device (the library
+ *    performs no device allocation of its own), which the caller keeps alive
+ *    until cdg_destroy.
+ *  - DG coefficient vectors are element-major [element][n_p], coefficients of
+ *    the orthonormalised scaled-monomial basis of each element (R2: monomials
+ *    of degree <= p in (x - c)/h, graded order, orthonormalised by Cholesky).
+ *    In this basis the coefficient 2-norm is the L2 norm.
+ *  - "User order" is the caller's element order; "tree order" numbers every
+ *    level so that the children of each agglomerate are contiguous
+ *    (cdg_export_level gives the permutation).  Per-level entry points use
+ *    tree order; cdg_solve / cdg_rhs use user order.
+ *  - Device entry points take device pointers and a cudaStream_t passed as
+ *    void* (NULL = legacy default stream) and are asynchronous unless stated.
+ */
+#ifndef CDG_H_
+#define CDG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDG_OK 0
+#define CDG_EINVAL 1      /* null pointer, bad size or option */
+#define CDG_EMESH 2       /* degenerate element, non-manifold face, no Dirichlet boundary */
+#define CDG_ENOCONV 3     /* maxit reached; outputs are still written */
+#define CDG_EBREAKDOWN 4  /* p^T A p <= 0 or a non-finite residual in CG */
+#define CDG_ECUDA 5       /* a CUDA runtime call failed */
+#define CDG_ETIMEOUT 6    /* a bounded device wait expired */
+#define CDG_ENOMEM 7      /* host allocation failed or device buffer too small */
+#define CDG_ESTATE 8      /* call out of order (e.g. solve before cdg_bind_device) */
+
+typedef struct cdg_handle cdg_handle;
+
+/* Mesh of simplices (Section 2.2: meshes T_h = {K}).  Boundary faces missing
+ * from bface are Dirichlet.  Element orientation is free. */
+typedef struct {
+  int32_t dim;              /* 2 (triangles) or 3 (tetrahedra) */
+  int64_t n_vertices;
+  const double* xyz;        /* [n_vertices][dim] */
+  int64_t n_elements;
+  const int64_t* elem;      /* [n_elements][dim+1] vertex ids */
+  int64_t n_bfaces;         /* may be 0 */
+  const int64_t* bface;     /* [n_bfaces][dim] vertex ids */
+  const int32_t* btag;      /* [n_bfaces] 0 = Dirichlet, 1 = Neumann */
+} cdg_mesh;
+
+typedef struct {
+  int32_t p;                /* polynomial degree >= 1 (n_p = C(p+d, d)) */
+  double gamma;             /* C_D = gamma / h_avg (Section 2.2), default 1e4 */
+  int32_t nu_pre, nu_post;  /* smoothing steps; equal values give a symmetric V-cycle */
+  double omega;             /* block-Jacobi damping, default 2/3 (Section 4.3) */
+  int32_t max_levels;       /* levels including level 0 (Algorithm 1 stops earlier at 1 element) */
+  uint64_t seed;            /* tie-break seed of Algorithm 2 */
+  int32_t precision;        /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 CG */
+  int32_t switch_kind;      /* 0: directional consistent switch, 1: natural switch (Section 2.2) */
+  const int8_t* face_switch;   /* nullable: S_{K1}^{K2} per interior face (library face order) */
+  const int64_t* enumeration;  /* nullable: element enumeration N(K) of the natural switch */
+  const double* kappa;         /* nullable: per-element diffusion coefficient (user order) */
+  int32_t coarsen;          /* 0: flux coarsening (Section 4.1), 1: primal A_{l+1} = R A_l L */
+  double tol;               /* relative residual ||r||/||b|| to stop CG, default 1e-10 */
+  int32_t maxit;            /* CG iteration limit, default 500 */
+} cdg_options;
+
+#define CDG_MAX_LEVELS 16
+
+typedef struct {
+  int32_t dim, p, n_p, n_levels;
+  int32_t nq;               /* volume quadrature points per element */
+  int32_t nfq;              /* quadrature points per face */
+  int64_t n_elements, n_interior_faces, n_bfaces, n_dofs;
+  int64_t n_l[CDG_MAX_LEVELS];      /* elements per level */
+  int64_t nnzb_l[CDG_MAX_LEVELS];   /* stored n_p x n_p blocks of A_l */
+  double h_avg, C_D;
+  int64_t device_bytes;     /* size of the buffer cdg_bind_device needs */
+  double setup_seconds[4];  /* mesh, level-0 assembly, agglomeration, coarsening */
+} cdg_info;
+
+/* Defaults: p=2, gamma=1e4, V(1,1), omega=2/3, 4 levels, seed 0, FP64,
+ * directional switch, flux coarsening, tol=1e-10, maxit=500. */
+void cdg_default_options(cdg_options* opt);
+
+/* Host set-up (Sections 2-4.1): faces, switch, quadrature, bases, level-0 CDG
+ * operator, Algorithm 2 hierarchy, transfers, flux-coarsened operators, block
+ * inverses and the dense inverse of the coarsest operator.  Copies all inputs.
+ * Errors: CDG_EINVAL, CDG_EMESH, CDG_ENOMEM. */
+int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out);
+void cdg_destroy(cdg_handle* h);
+const char* cdg_last_error(const cdg_handle* h);
+int cdg_query(const cdg_handle* h, cdg_info* info);
+
+/* Quadrature points at which the caller samples f, g_D and g_N (R3: collapsed
+ * Gauss-Legendre rules of degree 2p): xq [n_elements][nq][dim] in user order,
+ * xbq [n_bfaces][nfq][dim] in library boundary-face order (sorted by element,
+ * then local face), btag [n_bfaces].  Any pointer may be NULL. */
+int cdg_quadrature_points(const cdg_handle* h, double* xq, double* xbq, int32_t* btag);
+
+/* Host copies of the set-up, for inspection and tests (any pointer may be
+ * NULL).  perm [n_l]: tree position -> working index (level 0: user element);
+ * parent [n_l] (tree order, -1 on the coarsest level); A_l in tree order as
+ * BSR: rowptr [n_l+1], col [nnzb_l], val [nnzb_l][n_p][n_p] row-major blocks;
+ * transfer blocks L [n_l][n_p][n_p] with L_K = int_K phi_K psi_parent^T. */
+int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t* parent,
+                     int64_t* rowptr, int32_t* col, double* val, double* L);
+/* Agglomeration of one level in working numbering (Algorithm 2 output):
+ * parent [n_l] = index of the agglomerate on level l+1 in creation order. */
+int cdg_export_agglomeration(const cdg_handle* h, int32_t level, int64_t* parent);
+
+/* Device binding: copies the hierarchy into dev_buffer (>= info.device_bytes
+ * bytes, 256-byte aligned) on stream and synchronises it.  Errors: CDG_ENOMEM
+ * (buffer too small), CDG_ECUDA. */
+int cdg_bind_device(cdg_handle* h, void* dev_buffer, int64_t bytes, void* stream);
+
+/* Right-hand side b (user order, [n_elements][n_p]) from f at the volume
+ * points [n_elements][nq] and g_D, g_N at the boundary points
+ * [n_bfaces][nfq] (NULL = zero), all device pointers:
+ * b = int f v + int_{Gamma_D} kappa g_D (-dv/dn + C_D v) + int_{Gamma_N} g_N v. */
+int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD_q, const double* gN_q, double* b,
+            void* stream);
+
+/* Full solve (Section 4, Section 5 set-up): b from (f, g_D, g_N), then CG
+ * preconditioned by one V-cycle per iteration from u0 (u holds u0 on entry
+ * when use_u0 != 0, else u0 = 0) until ||r||/||b|| <= tol or maxit.  Writes u
+ * (user order), res_hist[0..iters] (relative recurrence residuals, array of
+ * maxit+1 entries) and *iters.  host_pointers != 0: f_q, gD_q, gN_q, u and
+ * res_hist are host arrays (copied in and out inside the call); else device
+ * arrays (res_hist may then be a host array too: it is always written from
+ * the host).  Synchronises stream.  Errors: CDG_ESTATE, CDG_ENOCONV,
+ * CDG_EBREAKDOWN, CDG_ECUDA. */
+int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double* gN_q, double* u,
+              int32_t use_u0, double* res_hist, int32_t* iters, int32_t host_pointers, void* stream);
+
+/* Same solve from a given load vector b (device, user order, [n_elements][n_p]). */
+int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist,
+                int32_t* iters, void* stream);
+
+/* Per-level operations (device pointers, tree order, FP64): */
+/* y = A_l x  (block-sparse apply, eq. primal_form and Section 4.1) */
+int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream);
+/* y = b - A_l x */
+int cdg_residual(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
+                 void* stream);
+/* y = x + omega D_l^{-1} (b - A_l x)  (damped block Jacobi, Section 4.3; y != x) */
+int cdg_smooth(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
+               void* stream);
+/* bc = R r = sum over children K of L_K^T r_K  (level -> level+1, Section 3.4) */
+int cdg_restrict(cdg_handle* h, int32_t level, const double* r, double* bc, void* stream);
+/* x += L xc  (level+1 -> level injection, Section 3.4) */
+int cdg_prolong(cdg_handle* h, int32_t level, const double* xc, double* x, void* stream);
+/* x = A_n^{-1} b on the coarsest level (dense inverse, Section 4.3) */
+int cdg_coarse_solve(cdg_handle* h, const double* b, double* x, void* stream);
+/* z = V(r): one V(nu_pre, nu_post) cycle on level 0 from a zero guess (R14),
+ * in the handle's precision; r, z FP64 tree order. */
+int cdg_vcycle(cdg_handle* h, const double* r, double* z, void* stream);
+/* Permutations between user and tree order of level 0 (device). */
+int cdg_to_tree(cdg_handle* h, const double* user, double* tree, void* stream);
+int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDG_H_ */

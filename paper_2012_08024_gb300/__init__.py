@@ -1,0 +1,280 @@
+"""GB300 agglomeration h-multigrid for Compact DG discretisations of Poisson's
+equation (Pan & Persson, arXiv 2012.08024) -- Python binding of libcdgmg.so.
+
+The binding only marshals arguments: the host set-up (Sections 2-4.1) runs in
+the library's C++ code and every step of the solve phase (Section 4) runs in its
+CUDA kernels.  PyTorch provides the device buffer and the stream.  There is no
+fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdgmg.so")
+
+CDG_MAX_LEVELS = 16
+ERRORS = {1: "EINVAL", 2: "EMESH", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA", 6: "ETIMEOUT",
+          7: "ENOMEM", 8: "ESTATE"}
+
+
+class CdgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class cdg_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("xyz", C.c_void_p),
+                ("n_elements", C.c_int64), ("elem", C.c_void_p), ("n_bfaces", C.c_int64),
+                ("bface", C.c_void_p), ("btag", C.c_void_p)]
+
+
+class cdg_options(C.Structure):
+    _fields_ = [("p", C.c_int32), ("gamma", C.c_double), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
+                ("omega", C.c_double), ("max_levels", C.c_int32), ("seed", C.c_uint64),
+                ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
+                ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
+                ("tol", C.c_double), ("maxit", C.c_int32)]
+
+
+class cdg_info(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("p", C.c_int32), ("n_p", C.c_int32), ("n_levels", C.c_int32),
+                ("nq", C.c_int32), ("nfq", C.c_int32), ("n_elements", C.c_int64),
+                ("n_interior_faces", C.c_int64), ("n_bfaces", C.c_int64), ("n_dofs", C.c_int64),
+                ("n_l", C.c_int64 * CDG_MAX_LEVELS), ("nnzb_l", C.c_int64 * CDG_MAX_LEVELS),
+                ("h_avg", C.c_double), ("C_D", C.c_double), ("device_bytes", C.c_int64),
+                ("setup_seconds", C.c_double * 4)]
+
+
+_lib = None
+
+# every exported symbol with its argument types (checked against include/cdg.h by the tests)
+_P, _I32, _I64, _D, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
+SIGNATURES = {
+    "cdg_default_options": (None, [_P]),
+    "cdg_create": (_I32, [_P, _P, _P]),
+    "cdg_destroy": (None, [_P]),
+    "cdg_last_error": (C.c_char_p, [_P]),
+    "cdg_query": (_I32, [_P, _P]),
+    "cdg_quadrature_points": (_I32, [_P, _P, _P, _P]),
+    "cdg_export_level": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P]),
+    "cdg_export_agglomeration": (_I32, [_P, _I32, _P]),
+    "cdg_bind_device": (_I32, [_P, _P, _I64, _P]),
+    "cdg_rhs": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "cdg_solve": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P]),
+    "cdg_solve_b": (_I32, [_P, _P, _P, _I32, _P, _P, _P]),
+    "cdg_apply": (_I32, [_P, _I32, _P, _P, _P]),
+    "cdg_residual": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "cdg_smooth": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "cdg_restrict": (_I32, [_P, _I32, _P, _P, _P]),
+    "cdg_prolong": (_I32, [_P, _I32, _P, _P, _P]),
+    "cdg_coarse_solve": (_I32, [_P, _P, _P, _P]),
+    "cdg_vcycle": (_I32, [_P, _P, _P, _P]),
+    "cdg_to_tree": (_I32, [_P, _P, _P, _P]),
+    "cdg_to_user": (_I32, [_P, _P, _P, _P]),
+}
+
+
+def lib():
+    """Loads libcdgmg.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2012_08024_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()        # torch tensor
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+PRECISION = {"fp64": 0, "fp32": 1}
+COARSEN = {"flux": 0, "primal": 1}
+
+
+class Solver:
+    """Host set-up of one mesh (cdg_create) plus its device solve phase."""
+
+    def __init__(self, mesh, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
+                 omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
+                 switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
+                 coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500):
+        L = lib()
+        self._keep = []
+        xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+        elem = np.ascontiguousarray(mesh.elem, dtype=np.int64)
+        bface = np.ascontiguousarray(mesh.bface, dtype=np.int64).reshape(-1, mesh.dim)
+        btag = np.ascontiguousarray(mesh.btag, dtype=np.int32)
+        m = cdg_mesh(mesh.dim, xyz.shape[0], xyz.ctypes.data, elem.shape[0], elem.ctypes.data,
+                     bface.shape[0], bface.ctypes.data if len(bface) else None,
+                     btag.ctypes.data if len(btag) else None)
+        o = cdg_options()
+        L.cdg_default_options(C.byref(o))
+        o.p, o.gamma, o.nu_pre, o.nu_post, o.omega = p, gamma, nu_pre, nu_post, omega
+        o.max_levels, o.seed = max_levels, seed
+        o.precision, o.switch_kind = PRECISION[precision], switch_kind
+        o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
+        arrs = {}
+        if face_switch is not None:
+            arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)
+            o.face_switch = arrs["fs"].ctypes.data
+        if enumeration is not None:
+            arrs["en"] = np.ascontiguousarray(enumeration, dtype=np.int64)
+            o.enumeration = arrs["en"].ctypes.data
+        if kappa is not None:
+            arrs["ka"] = np.ascontiguousarray(kappa, dtype=np.float64)
+            o.kappa = arrs["ka"].ctypes.data
+        h = C.c_void_p()
+        rc = L.cdg_create(C.byref(m), C.byref(o), C.byref(h))
+        if rc:
+            raise CdgError(rc, L.cdg_last_error(None).decode())
+        self._h = h
+        self.precision = precision
+        self.buffer = None
+        inf = cdg_info()
+        L.cdg_query(h, C.byref(inf))
+        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l") else
+                         list(getattr(inf, k)) if k == "setup_seconds" else getattr(inf, k))
+                     for k, _ in cdg_info._fields_}
+        self.np_ = inf.n_p
+        self.n_levels = inf.n_levels
+        self.ne = inf.n_elements
+        self.maxit = maxit
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.cdg_destroy(h)
+            self._h = None
+
+    def _check(self, rc):
+        if rc:
+            raise CdgError(rc, lib().cdg_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- host side
+    def quadrature_points(self):
+        d, ne, nbf = self.info["dim"], self.ne, self.info["n_bfaces"]
+        xq = np.empty((ne, self.info["nq"], d))
+        xbq = np.empty((nbf, self.info["nfq"], d))
+        btag = np.empty(nbf, dtype=np.int32)
+        self._check(lib().cdg_quadrature_points(self._h, xq.ctypes.data, xbq.ctypes.data, btag.ctypes.data))
+        return xq, xbq, btag
+
+    def export_level(self, level: int):
+        n = self.info["n_l"][level]
+        nnzb = self.info["nnzb_l"][level]
+        npb = self.np_
+        out = dict(perm=np.empty(n, dtype=np.int64), parent=np.empty(n, dtype=np.int32),
+                   rowptr=np.empty(n + 1, dtype=np.int64), col=np.empty(nnzb, dtype=np.int32),
+                   val=np.empty((nnzb, npb, npb)), L=np.zeros((n, npb, npb)))
+        self._check(lib().cdg_export_level(self._h, level, *(out[k].ctypes.data for k in
+                                                             ("perm", "parent", "rowptr", "col", "val", "L"))))
+        return out
+
+    def export_agglomeration(self, level: int):
+        par = np.empty(self.info["n_l"][level], dtype=np.int64)
+        self._check(lib().cdg_export_agglomeration(self._h, level, par.ctypes.data))
+        return par
+
+    # ---------------------------------------------------------------- device side
+    def bind(self, device="cuda"):
+        import torch
+        nbytes = int(self.info["device_bytes"])
+        self.buffer = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.buffer.data_ptr()
+        aligned = (base + 255) & ~255
+        self._check(lib().cdg_bind_device(self._h, aligned, nbytes, _stream_ptr(None)))
+        return self
+
+    def _dev(self, x):
+        return _ptr(x)
+
+    def solve(self, f_q, gD=None, gN=None, u0=None, stream=None):
+        """Device tensors in user order; returns (u, residual history, iterations)."""
+        import torch
+        u = torch.empty((self.ne, self.np_), dtype=torch.float64, device=f_q.device) if u0 is None else u0
+        hist = np.zeros(self.maxit + 1)
+        it = C.c_int32(0)
+        rc = lib().cdg_solve(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(u), 0 if u0 is None else 1,
+                             hist.ctypes.data, C.byref(it), 0, _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return u, hist[:it.value + 1], it.value, rc
+
+    def solve_host(self, f_q: np.ndarray, gD=None, gN=None, stream=None):
+        """Host numpy arrays in and out (copies inside the call)."""
+        f_q = np.ascontiguousarray(f_q, dtype=np.float64)
+        gD = None if gD is None else np.ascontiguousarray(gD, dtype=np.float64)
+        gN = None if gN is None else np.ascontiguousarray(gN, dtype=np.float64)
+        u = np.empty((self.ne, self.np_))
+        hist = np.zeros(self.maxit + 1)
+        it = C.c_int32(0)
+        rc = lib().cdg_solve(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(u), 0, hist.ctypes.data,
+                             C.byref(it), 1, _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return u, hist[:it.value + 1], it.value, rc
+
+    def solve_b(self, b, stream=None):
+        import torch
+        u = torch.empty((self.ne, self.np_), dtype=torch.float64, device=b.device)
+        hist = np.zeros(self.maxit + 1)
+        it = C.c_int32(0)
+        rc = lib().cdg_solve_b(self._h, _ptr(b), _ptr(u), 0, hist.ctypes.data, C.byref(it), _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return u, hist[:it.value + 1], it.value, rc
+
+    def rhs(self, f_q, gD=None, gN=None, stream=None):
+        import torch
+        b = torch.empty((self.ne, self.np_), dtype=torch.float64, device=f_q.device)
+        self._check(lib().cdg_rhs(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(b), _stream_ptr(stream)))
+        return b
+
+    def apply(self, level, x, y, stream=None):
+        self._check(lib().cdg_apply(self._h, level, _ptr(x), _ptr(y), _stream_ptr(stream)))
+
+    def residual(self, level, x, b, y, stream=None):
+        self._check(lib().cdg_residual(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+
+    def smooth(self, level, x, b, y, stream=None):
+        self._check(lib().cdg_smooth(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+
+    def restrict(self, level, r, bc, stream=None):
+        self._check(lib().cdg_restrict(self._h, level, _ptr(r), _ptr(bc), _stream_ptr(stream)))
+
+    def prolong(self, level, xc, x, stream=None):
+        self._check(lib().cdg_prolong(self._h, level, _ptr(xc), _ptr(x), _stream_ptr(stream)))
+
+    def coarse_solve(self, b, x, stream=None):
+        self._check(lib().cdg_coarse_solve(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
+
+    def vcycle(self, r, z, stream=None):
+        self._check(lib().cdg_vcycle(self._h, _ptr(r), _ptr(z), _stream_ptr(stream)))
+
+    def to_tree(self, user, tree, stream=None):
+        self._check(lib().cdg_to_tree(self._h, _ptr(user), _ptr(tree), _stream_ptr(stream)))
+
+    def to_user(self, tree, user, stream=None):
+        self._check(lib().cdg_to_user(self._h, _ptr(tree), _ptr(user), _stream_ptr(stream)))

@@ -1,0 +1,287 @@
+// C ABI entry points (include/cdg.h): host set-up, queries and exports; the
+// device entry points forward to device.cu.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "handle.h"
+
+namespace {
+thread_local std::string g_create_error;
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int fail(cdg_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+}  // namespace
+
+extern "C" {
+
+void cdg_default_options(cdg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->p = 2;
+  o->gamma = 1e4;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->omega = 2.0 / 3.0;
+  o->max_levels = 4;
+  o->seed = 0;
+  o->precision = 0;
+  o->switch_kind = 0;
+  o->coarsen = 0;
+  o->tol = 1e-10;
+  o->maxit = 500;
+}
+
+const char* cdg_last_error(const cdg_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out) {
+  if (!out) return fail(nullptr, CDG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !opt) return fail(nullptr, CDG_EINVAL, "mesh or options NULL");
+  if (opt->p < 1 || opt->p > 6) return fail(nullptr, CDG_EINVAL, "p must be in [1, 6]");
+  if (opt->max_levels < 1 || opt->max_levels > CDG_MAX_LEVELS)
+    return fail(nullptr, CDG_EINVAL, "max_levels must be in [1, 16]");
+  if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->nu_pre + opt->nu_post < 1)
+    return fail(nullptr, CDG_EINVAL, "need nu_pre, nu_post >= 0 and at least one smoothing step");
+  if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0))
+    return fail(nullptr, CDG_EINVAL, "bad omega, gamma, tol or maxit");
+  if (opt->precision < 0 || opt->precision > 1) return fail(nullptr, CDG_EINVAL, "precision must be 0 or 1");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, CDG_EINVAL, "dim must be 2 or 3");
+  if (mesh->n_elements <= 0 || mesh->n_vertices <= 0 || !mesh->xyz || !mesh->elem)
+    return fail(nullptr, CDG_EINVAL, "empty mesh");
+  if (mesh->n_bfaces < 0 || (mesh->n_bfaces > 0 && !mesh->bface))
+    return fail(nullptr, CDG_EINVAL, "bad boundary face list");
+  cdg_handle* h = nullptr;
+  try {
+    h = new cdg_handle();
+    h->opt = *opt;
+    h->opt.face_switch = nullptr;
+    h->opt.enumeration = nullptr;
+    h->opt.kappa = nullptr;
+    cdg::Hierarchy& H = h->H;
+    cdg::Options& o = H.opt;
+    o.p = opt->p;
+    o.gamma = opt->gamma;
+    o.nu_pre = opt->nu_pre;
+    o.nu_post = opt->nu_post;
+    o.omega = opt->omega;
+    o.max_levels = opt->max_levels;
+    o.seed = opt->seed;
+    o.switch_kind = opt->switch_kind;
+    o.coarsen = opt->coarsen;
+    const int64_t ne = mesh->n_elements;
+    if (opt->enumeration) o.enumeration.assign(opt->enumeration, opt->enumeration + ne);
+    if (opt->kappa) {
+      o.kappa.assign(opt->kappa, opt->kappa + ne);
+      for (double k : o.kappa)
+        if (!(k > 0) || !std::isfinite(k)) {
+          delete h;
+          return fail(nullptr, CDG_EINVAL, "kappa must be positive and finite");
+        }
+    }
+    double t0 = now();
+    cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces,
+                    mesh->bface, mesh->btag, o, H.mesh);
+    if (opt->face_switch) {
+      const size_t nif = H.mesh.if_K1.size();
+      o.face_switch.assign(opt->face_switch, opt->face_switch + nif);
+      cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces,
+                      mesh->bface, mesh->btag, o, H.mesh);
+    }
+    H.mono.init(mesh->dim, o.p);
+    H.np = H.mono.np;
+    H.vrule = cdg::simplex_rule(mesh->dim, 2 * o.p);
+    H.frule = cdg::simplex_rule(mesh->dim - 1, 2 * o.p);
+    H.lev.assign(1, cdg::Level());
+    double t1 = now();
+    cdg::build_level0(H);
+    double t2 = now();
+    cdg::agglomerate(H);
+    double t3 = now();
+    cdg::coarsen(H);
+    cdg::finalize_tree_order(H);
+    cdg::build_rhs_data(H);
+    double t4 = now();
+    H.t_mesh = t1 - t0;
+    H.t_assemble = t2 - t1;
+    H.t_agglomerate = t3 - t2;
+    H.t_coarsen = t4 - t3;
+  } catch (const std::invalid_argument& e) {
+    delete h;
+    return fail(nullptr, CDG_EINVAL, e.what());
+  } catch (const std::domain_error& e) {
+    delete h;
+    return fail(nullptr, CDG_EMESH, e.what());
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(nullptr, CDG_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    delete h;
+    return fail(nullptr, CDG_EMESH, e.what());
+  }
+  *out = h;
+  return CDG_OK;
+}
+
+void cdg_destroy(cdg_handle* h) {
+  if (!h) return;
+  dev_release(h);
+  delete h;
+}
+
+int cdg_query(const cdg_handle* h, cdg_info* info) {
+  if (!h || !info) return CDG_EINVAL;
+  const cdg::Hierarchy& H = h->H;
+  std::memset(info, 0, sizeof(*info));
+  info->dim = H.mesh.d;
+  info->p = H.opt.p;
+  info->n_p = H.np;
+  info->n_levels = (int32_t)H.lev.size();
+  info->nq = H.vrule.n();
+  info->nfq = H.frule.n();
+  info->n_elements = H.mesh.ne;
+  info->n_interior_faces = (int64_t)H.mesh.if_K1.size();
+  info->n_bfaces = (int64_t)H.mesh.bf_K.size();
+  info->n_dofs = H.mesh.ne * H.np;
+  for (size_t l = 0; l < H.lev.size(); ++l) {
+    info->n_l[l] = H.lev[l].n;
+    info->nnzb_l[l] = H.A_t[l].nnzb();
+  }
+  info->h_avg = H.mesh.h_avg;
+  info->C_D = H.mesh.C_D;
+  int64_t b = 0;
+  dev_bytes(h, &b);
+  info->device_bytes = b;
+  info->setup_seconds[0] = H.t_mesh;
+  info->setup_seconds[1] = H.t_assemble;
+  info->setup_seconds[2] = H.t_agglomerate;
+  info->setup_seconds[3] = H.t_coarsen;
+  return CDG_OK;
+}
+
+int cdg_quadrature_points(const cdg_handle* h, double* xq, double* xbq, int32_t* btag) {
+  if (!h) return CDG_EINVAL;
+  const cdg::Hierarchy& H = h->H;
+  const cdg::Mesh0& m = H.mesh;
+  const int d = m.d;
+  if (xq) {
+    const int nq = H.vrule.n();
+    for (int64_t K = 0; K < m.ne; ++K) {
+      const int64_t* ev = m.elem.data() + K * (d + 1);
+      for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < d; ++k) {
+          double s = m.xyz[ev[0] * d + k];
+          for (int i = 0; i < d; ++i)
+            s += H.vrule.x[(size_t)q * d + i] * (m.xyz[ev[i + 1] * d + k] - m.xyz[ev[0] * d + k]);
+          xq[((size_t)K * nq + q) * d + k] = s;
+        }
+    }
+  }
+  const int nfq = H.frule.n();
+  for (size_t b = 0; b < m.bf_K.size(); ++b) {
+    if (btag) btag[b] = m.bf_tag[b];
+    if (!xbq) continue;
+    const double* xv = &m.bf_xv[b * d * d];
+    for (int q = 0; q < nfq; ++q)
+      for (int k = 0; k < d; ++k) {
+        double s = xv[k];
+        for (int i = 0; i < d - 1; ++i) s += H.frule.x[(size_t)q * (d - 1) + i] * (xv[(i + 1) * d + k] - xv[k]);
+        xbq[((size_t)b * nfq + q) * d + k] = s;
+      }
+  }
+  return CDG_OK;
+}
+
+int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t* parent, int64_t* rowptr,
+                     int32_t* col, double* val, double* L) {
+  if (!h) return CDG_EINVAL;
+  const cdg::Hierarchy& H = h->H;
+  if (level < 0 || level >= (int32_t)H.lev.size()) return CDG_EINVAL;
+  const int64_t n = H.lev[level].n;
+  const cdg::BSR& A = H.A_t[level];
+  const size_t nb2 = (size_t)H.np * H.np;
+  const bool last = level + 1 == (int32_t)H.lev.size();
+  if (perm) std::memcpy(perm, H.order[level].data(), sizeof(int64_t) * n);
+  if (parent)
+    for (int64_t k = 0; k < n; ++k) parent[k] = last ? -1 : H.parent_t[level][k];
+  if (rowptr) std::memcpy(rowptr, A.rowptr.data(), sizeof(int64_t) * (n + 1));
+  if (col) std::memcpy(col, A.col.data(), sizeof(int32_t) * A.col.size());
+  if (val) std::memcpy(val, A.val.data(), sizeof(double) * A.val.size());
+  if (L && !last) std::memcpy(L, H.L_t[level].data(), sizeof(double) * n * nb2);
+  return CDG_OK;
+}
+
+int cdg_export_agglomeration(const cdg_handle* h, int32_t level, int64_t* parent) {
+  if (!h || !parent) return CDG_EINVAL;
+  const cdg::Hierarchy& H = h->H;
+  if (level < 0 || level + 1 >= (int32_t)H.lev.size()) return CDG_EINVAL;
+  std::memcpy(parent, H.lev[level].parent.data(), sizeof(int64_t) * H.lev[level].n);
+  return CDG_OK;
+}
+
+int cdg_bind_device(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
+  if (!h || !buf) return h ? fail(h, CDG_EINVAL, "buffer is NULL") : CDG_EINVAL;
+  return dev_bind(h, buf, bytes, stream);
+}
+
+int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b, void* stream) {
+  if (!h || !f_q || !b) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  return dev_rhs(h, f_q, gD, gN, b, true, stream);
+}
+
+int cdg_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* u, int32_t use_u0,
+              double* res_hist, int32_t* iters, int32_t host_pointers, void* stream) {
+  if (!h || !f_q || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  int it = 0;
+  int rc = dev_solve(h, f_q, gD, gN, nullptr, u, use_u0, res_hist, &it, host_pointers, stream);
+  if (iters) *iters = it;
+  return rc;
+}
+
+int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist, int32_t* iters,
+                void* stream) {
+  if (!h || !b || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  int it = 0;
+  int rc = dev_solve(h, nullptr, nullptr, nullptr, b, u, use_u0, res_hist, &it, 0, stream);
+  if (iters) *iters = it;
+  return rc;
+}
+
+int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream) {
+  return dev_level_op(h, 0, level, x, nullptr, y, stream);
+}
+int cdg_residual(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
+  return dev_level_op(h, 1, level, x, b, y, stream);
+}
+int cdg_smooth(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
+  return dev_level_op(h, 2, level, x, b, y, stream);
+}
+int cdg_restrict(cdg_handle* h, int32_t level, const double* r, double* bc, void* stream) {
+  return dev_level_op(h, 3, level, r, nullptr, bc, stream);
+}
+int cdg_prolong(cdg_handle* h, int32_t level, const double* xc, double* x, void* stream) {
+  return dev_level_op(h, 4, level, xc, nullptr, x, stream);
+}
+int cdg_coarse_solve(cdg_handle* h, const double* b, double* x, void* stream) {
+  return dev_level_op(h, 5, -1, b, nullptr, x, stream);
+}
+int cdg_vcycle(cdg_handle* h, const double* r, double* z, void* stream) { return dev_vcycle(h, r, z, stream); }
+int cdg_to_tree(cdg_handle* h, const double* user, double* tree, void* stream) {
+  return dev_permute(h, user, tree, true, stream);
+}
+int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream) {
+  return dev_permute(h, tree, user, false, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,881 @@
+// Device side of the solve phase: block-sparse CDG operator apply, damped
+// block-Jacobi smoothing, restriction / prolongation between agglomerates and
+// their children, the dense coarsest solve, the V-cycle (R14) and the outer CG
+// (R15).  All device memory is carved from one caller-provided buffer.
+//
+// Layout in HBM (tree order: children of every agglomerate contiguous):
+//   A_l      BSR, int32 rowptr/col, n_p x n_p row-major blocks, FP64 (+FP32 copy)
+//   Dinv_l   [n_l][n_p][n_p] inverses of the diagonal blocks of A_l
+//   L_l      [n_l][n_p][n_p] prolongation blocks to level l from its parent
+//   vectors  [n_l][n_p] element-major
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+namespace {
+
+constexpr int kMaxLev = CDG_MAX_LEVELS;
+constexpr int kThreads = 256;
+constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
+
+enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZOLD, S_TMP, S_COUNT = 16 };
+
+struct DevLevel {
+  int n = 0;
+  int64_t nnzb = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* A = nullptr;
+  double* Dinv = nullptr;
+  double* L = nullptr;
+  int* parent = nullptr;
+  int* childptr = nullptr;   // children range of each element of this level (l >= 1)
+  float* A32 = nullptr;
+  float* Dinv32 = nullptr;
+  float* L32 = nullptr;
+  void* x = nullptr;         // V-cycle work vectors in the V-cycle precision
+  void* t = nullptr;
+  void* r = nullptr;
+  void* b = nullptr;
+};
+
+}  // namespace
+
+struct DeviceState {
+  char* base = nullptr;
+  int64_t bytes = 0;
+  int nlev = 0, np = 0, d = 0, nq = 0, nfq = 0, precision = 0;
+  int64_t ne = 0, ndofs = 0, nbf = 0;
+  DevLevel lev[kMaxLev];
+  double* coarse_inv = nullptr;
+  int nc = 0;
+  double* coarse_b = nullptr;   // FP64 staging of the coarsest right-hand side / solution
+  double* coarse_x = nullptr;
+  // rhs data
+  double* rhs_vol = nullptr;
+  int* rhs_bptr = nullptr;
+  int* rhs_bface = nullptr;
+  double* rhs_bdata = nullptr;
+  int* btag = nullptr;
+  int* perm0 = nullptr;         // tree row -> user element
+  // CG vectors (FP64, tree order)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr,
+         *zold = nullptr;
+  float *r32 = nullptr, *z32 = nullptr;
+  // staging for host-pointer solves
+  double *f_stage = nullptr, *gD_stage = nullptr, *gN_stage = nullptr, *u_stage = nullptr;
+  double* scal = nullptr;
+  double* partial = nullptr;
+  int npartial = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ layout
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base) {
+  Carver c{base};
+  const int np = H.np;
+  const size_t nb2 = (size_t)np * np;
+  const int nlev = (int)H.lev.size();
+  const int64_t ne = H.mesh.ne;
+  const size_t vecbytes_elems = (size_t)ne * np;
+  DeviceState tmp;
+  DeviceState& D = S ? *S : tmp;
+  D.nlev = nlev;
+  D.np = np;
+  D.d = H.mesh.d;
+  D.nq = H.vrule.n();
+  D.nfq = H.frule.n();
+  D.ne = ne;
+  D.ndofs = ne * np;
+  D.nbf = (int64_t)H.mesh.bf_K.size();
+  D.precision = precision;
+  const size_t vsz = precision ? sizeof(float) : sizeof(double);
+  for (int l = 0; l < nlev; ++l) {
+    DevLevel& L = D.lev[l];
+    const cdg::BSR& A = H.A_t[l];
+    L.n = (int)A.nrows;
+    L.nnzb = A.nnzb();
+    L.rowptr = c.take<int>(A.nrows + 1);
+    L.col = c.take<int>(A.nnzb());
+    const bool last = l + 1 == nlev;
+    // FP64 operator: level 0 always (outer CG); all levels in FP64 mode
+    if (l == 0 || precision == 0) L.A = c.take<double>(A.val.size());
+    if (!last) {
+      if (precision == 0) {
+        L.Dinv = c.take<double>((size_t)L.n * nb2);
+        L.L = c.take<double>((size_t)L.n * nb2);
+      } else {
+        L.A32 = c.take<float>(A.val.size());
+        L.Dinv32 = c.take<float>((size_t)L.n * nb2);
+        L.L32 = c.take<float>((size_t)L.n * nb2);
+      }
+      L.parent = c.take<int>(L.n);
+    }
+    if (l > 0) L.childptr = c.take<int>(L.n + 1);
+    const size_t nv = (size_t)L.n * np;
+    L.x = c.take<char>(nv * vsz);
+    L.t = c.take<char>(nv * vsz);
+    L.r = c.take<char>(nv * vsz);
+    L.b = c.take<char>(nv * vsz);
+  }
+  D.nc = (int)(H.lev.back().n * np);
+  D.coarse_inv = c.take<double>((size_t)D.nc * D.nc);
+  D.coarse_b = c.take<double>(D.nc);
+  D.coarse_x = c.take<double>(D.nc);
+  D.rhs_vol = c.take<double>(H.rhs_vol.size());
+  D.rhs_bptr = c.take<int>(H.rhs_bptr.size());
+  D.rhs_bface = c.take<int>(H.rhs_bface.size() + 1);
+  D.rhs_bdata = c.take<double>(H.rhs_bD.size() + 1);
+  D.btag = c.take<int>(D.nbf + 1);
+  D.perm0 = c.take<int>(ne);
+  D.x = c.take<double>(vecbytes_elems);
+  D.r = c.take<double>(vecbytes_elems);
+  D.z = c.take<double>(vecbytes_elems);
+  D.p = c.take<double>(vecbytes_elems);
+  D.q = c.take<double>(vecbytes_elems);
+  D.bt = c.take<double>(vecbytes_elems);
+  D.zold = c.take<double>(vecbytes_elems);
+  if (precision) {
+    D.r32 = c.take<float>(vecbytes_elems);
+    D.z32 = c.take<float>(vecbytes_elems);
+  }
+  D.f_stage = c.take<double>((size_t)ne * D.nq);
+  D.gD_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
+  D.gN_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
+  D.u_stage = c.take<double>(vecbytes_elems);
+  D.scal = c.take<double>(S_COUNT);
+  D.npartial = std::max<int>(kDotBlocks, (int)((int64_t)ne * np / 64 + 2));
+  D.partial = c.take<double>((size_t)D.npartial * 2);
+  return (c.off + 255) & ~size_t(255);
+}
+
+// ------------------------------------------------------------------ kernels
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// One thread per scalar row: lane = sub * NP + i handles row i of block row
+// warp * (32 / NP) + sub.  MODE 0: y = A x, 1: y = b - A x,
+// 2: y = x + omega Dinv (b - A x).  With dot != nullptr, MODE 0 also writes the
+// block partial of sum_i x_i y_i (for p^T A p).
+template <typename T, int NP, int MODE>
+__global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restrict__ rowptr,
+                                                       const int* __restrict__ col, const T* __restrict__ A,
+                                                       const T* __restrict__ Dinv, const T* __restrict__ x,
+                                                       const T* __restrict__ b, T* __restrict__ y, T omega,
+                                                       double* __restrict__ dot) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int K = warp * RPW + sub;
+  const bool active = (sub < RPW) && (K < n);
+  T acc = T(0);
+  if (active) {
+    const int b0 = rowptr[K], b1 = rowptr[K + 1];
+    for (int bb = b0; bb < b1; ++bb) {
+      const int J = ldg(col + bb);
+      const T* a = A + (size_t)bb * NP * NP + i * NP;
+      const T* xj = x + (size_t)J * NP;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
+    }
+  }
+  const size_t row = (size_t)K * NP + i;
+  if (MODE == 0) {
+    if (active) y[row] = acc;
+    if (dot) {
+      double v = active ? (double)x[row] * (double)acc : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      __shared__ double red[kThreads / 32];
+      if (lane == 0) red[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+        dot[blockIdx.x] = s;
+      }
+    }
+  } else {
+    const T r = active ? b[row] - acc : T(0);
+    if (MODE == 1) {
+      if (active) y[row] = r;
+    } else {
+      T s = T(0);
+      const T* D = Dinv + (size_t)(active ? K : 0) * NP * NP + i * NP;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const T rj = __shfl_sync(0xffffffffu, r, sub * NP + j);
+        if (active) s = fma(ldg(D + j), rj, s);
+      }
+      if (active) y[row] = x[row] + omega * s;
+    }
+  }
+}
+
+// x = omega Dinv b (first smoothing step from a zero guess)
+template <typename T, int NP>
+__global__ void __launch_bounds__(kThreads) smooth_zero_kernel(int n, const T* __restrict__ Dinv,
+                                                               const T* __restrict__ b, T* __restrict__ x,
+                                                               T omega) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int K = warp * RPW + sub;
+  if (sub >= RPW || K >= n) return;
+  const T* D = Dinv + (size_t)K * NP * NP + i * NP;
+  const T* bk = b + (size_t)K * NP;
+  T s = T(0);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) s = fma(ldg(D + j), ldg(bk + j), s);
+  x[(size_t)K * NP + i] = omega * s;
+}
+
+// bc[A] = sum over children K of L_K^T r[K]
+template <typename T, int NP>
+__global__ void __launch_bounds__(kThreads) restrict_kernel(int nc, const int* __restrict__ childptr,
+                                                            const T* __restrict__ L, const T* __restrict__ r,
+                                                            T* __restrict__ bc) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int Ag = warp * RPW + sub;
+  if (sub >= RPW || Ag >= nc) return;
+  T s = T(0);
+  for (int K = childptr[Ag]; K < childptr[Ag + 1]; ++K) {
+    const T* LK = L + (size_t)K * NP * NP + i;
+    const T* rk = r + (size_t)K * NP;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s = fma(ldg(LK + j * NP), ldg(rk + j), s);
+  }
+  bc[(size_t)Ag * NP + i] = s;
+}
+
+// x[K] (+)= L_K xc[parent K]
+template <typename T, int NP, bool ADD>
+__global__ void __launch_bounds__(kThreads) prolong_kernel(int n, const int* __restrict__ parent,
+                                                           const T* __restrict__ L, const T* __restrict__ xc,
+                                                           T* __restrict__ x) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int K = warp * RPW + sub;
+  if (sub >= RPW || K >= n) return;
+  const T* LK = L + (size_t)K * NP * NP + i * NP;
+  const T* xa = xc + (size_t)parent[K] * NP;
+  T s = T(0);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) s = fma(ldg(LK + j), ldg(xa + j), s);
+  const size_t row = (size_t)K * NP + i;
+  x[row] = ADD ? x[row] + s : s;
+}
+
+// dense symmetric inverse times vector: x[i] = sum_j Ainv[j][i] b[j] (FP64)
+template <typename TI, typename TO>
+__global__ void coarse_kernel(int nc, const double* __restrict__ Ainv, const TI* __restrict__ b,
+                              TO* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double s = 0.0;
+  for (int j = 0; j < nc; ++j) s = fma(Ainv[(size_t)j * nc + i], (double)b[j], s);
+  x[i] = (TO)s;
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(size_t n, const TI* __restrict__ a, TO* __restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (TO)a[i];
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// partial[blk] = sum x.y (and partial[npart + blk] = sum x.w when w != nullptr)
+__global__ void __launch_bounds__(kThreads) dot_kernel(size_t n, const double* __restrict__ x,
+                                                       const double* __restrict__ y, const double* __restrict__ w,
+                                                       double* __restrict__ partial, int npart) {
+  double s = 0.0, s2 = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    s = fma(x[i], y[i], s);
+    if (w) s2 = fma(x[i], w[i], s2);
+  }
+  s = block_sum(s);
+  if (w) s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    if (w) partial[npart + blockIdx.x] = s2;
+  }
+}
+
+// Sums partials in a fixed order and updates the CG scalars.
+// which: 0 -> PQ (alpha = RZ/PQ), 1 -> RR, 2 -> RZ (beta, Fletcher-Reeves or,
+// when flexible, Polak-Ribiere with the second partial = (r_new, z_old)), 3 -> BB
+__global__ void finalize_kernel(const double* __restrict__ partial, int cnt, int npart, int which,
+                                int flexible, double* __restrict__ scal) {
+  __shared__ double red[kThreads / 32];
+  double s = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    s += partial[i];
+    if (which == 2 && flexible) s2 += partial[npart + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kThreads / 32; ++w) tot += red[w];
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot2 = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) tot2 += red[w];
+    if (which == 0) {
+      scal[S_PQ] = tot;
+      scal[S_ALPHA] = scal[S_RZ] / tot;
+    } else if (which == 1) {
+      scal[S_RR] = tot;
+    } else if (which == 2) {
+      const double rz_old = scal[S_RZ];
+      scal[S_BETA] = flexible ? (tot - tot2) / rz_old : tot / rz_old;
+      scal[S_RZ] = tot;
+    } else {
+      scal[S_BB] = tot;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; partial of r.r
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(size_t n, const double* __restrict__ scal,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ q, double* __restrict__ x,
+                                                             double* __restrict__ r, double* __restrict__ partial) {
+  const double alpha = scal[S_ALPHA];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// p = z + beta p (beta = 0: p = z)
+__global__ void __launch_bounds__(kThreads) cg_p_kernel(size_t n, const double* __restrict__ scal, int first,
+                                                        const double* __restrict__ z, double* __restrict__ p) {
+  const double beta = first ? 0.0 : scal[S_BETA];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+}
+
+// b (tree order, or user order) from f at volume points and g_D / g_N at boundary points
+template <int NP>
+__global__ void __launch_bounds__(kThreads) rhs_kernel(int ne, int nq, int nfq, const int* __restrict__ perm0,
+                                                       const double* __restrict__ V, const double* __restrict__ f,
+                                                       const int* __restrict__ bptr, const int* __restrict__ bface,
+                                                       const double* __restrict__ bdata, const int* __restrict__ btag,
+                                                       const double* __restrict__ gD, const double* __restrict__ gN,
+                                                       double* __restrict__ b, int user_out) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int k = warp * RPW + sub;
+  if (sub >= RPW || k >= ne) return;
+  const int K = perm0[k];
+  double s = 0.0;
+  const double* Vk = V + (size_t)k * nq * NP + i;
+  const double* fk = f + (size_t)K * nq;
+  for (int q = 0; q < nq; ++q) s = fma(Vk[(size_t)q * NP], fk[q], s);
+  for (int t = bptr[k]; t < bptr[k + 1]; ++t) {
+    const int bf = bface[t];
+    const double* g = btag[bf] == 0 ? gD : gN;
+    if (!g) continue;
+    const double* Bd = bdata + (size_t)bf * nfq * NP + i;
+    for (int q = 0; q < nfq; ++q) s = fma(Bd[(size_t)q * NP], g[(size_t)bf * nfq + q], s);
+  }
+  b[(size_t)(user_out ? K : k) * NP + i] = s;
+}
+
+__global__ void permute_kernel(int ne, int np, const int* __restrict__ perm0, const double* __restrict__ in,
+                               double* __restrict__ out, int to_tree) {
+  const size_t n = (size_t)ne * np;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = t / np, i = t - k * np;
+    const size_t K = perm0[k];
+    if (to_tree) out[k * np + i] = in[K * np + i];
+    else out[K * np + i] = in[k * np + i];
+  }
+}
+
+// ------------------------------------------------------------------ launch helpers
+inline unsigned rows_grid(int64_t nrows, int np) {
+  const int64_t rpw = 32 / np;
+  const int64_t warps = (nrows + rpw - 1) / rpw;
+  return (unsigned)std::max<int64_t>(1, (warps * 32 + kThreads - 1) / kThreads);
+}
+
+#define CDG_NP_DISPATCH(NPV, ...)                          \
+  switch (NPV) {                                           \
+    case 3: { constexpr int NP = 3; __VA_ARGS__; break; }  \
+    case 4: { constexpr int NP = 4; __VA_ARGS__; break; }  \
+    case 6: { constexpr int NP = 6; __VA_ARGS__; break; }  \
+    case 10: { constexpr int NP = 10; __VA_ARGS__; break; } \
+    case 15: { constexpr int NP = 15; __VA_ARGS__; break; } \
+    case 20: { constexpr int NP = 20; __VA_ARGS__; break; } \
+    case 21: { constexpr int NP = 21; __VA_ARGS__; break; } \
+    case 28: { constexpr int NP = 28; __VA_ARGS__; break; } \
+    default: return false;                                 \
+  }
+
+template <typename T>
+bool launch_bsr(int mode, int np, const DevLevel& L, const T* A, const T* Dinv, const T* x, const T* b, T* y,
+                double omega, double* dot, cudaStream_t s) {
+  const unsigned g = rows_grid(L.n, np);
+  CDG_NP_DISPATCH(np, {
+    if (mode == 0)
+      bsr_kernel<T, NP, 0><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, dot);
+    else if (mode == 1)
+      bsr_kernel<T, NP, 1><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, nullptr);
+    else
+      bsr_kernel<T, NP, 2><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, nullptr);
+  });
+  return true;
+}
+
+template <typename T>
+bool launch_smooth_zero(int np, int n, const T* Dinv, const T* b, T* x, double omega, cudaStream_t s) {
+  CDG_NP_DISPATCH(np, smooth_zero_kernel<T, NP><<<rows_grid(n, np), kThreads, 0, s>>>(n, Dinv, b, x, (T)omega));
+  return true;
+}
+
+template <typename T>
+bool launch_restrict(int np, int nc, const int* cp, const T* L, const T* r, T* bc, cudaStream_t s) {
+  CDG_NP_DISPATCH(np, restrict_kernel<T, NP><<<rows_grid(nc, np), kThreads, 0, s>>>(nc, cp, L, r, bc));
+  return true;
+}
+
+template <typename T>
+bool launch_prolong(int np, int n, const int* parent, const T* L, const T* xc, T* x, bool add, cudaStream_t s) {
+  CDG_NP_DISPATCH(np, {
+    if (add) prolong_kernel<T, NP, true><<<rows_grid(n, np), kThreads, 0, s>>>(n, parent, L, xc, x);
+    else prolong_kernel<T, NP, false><<<rows_grid(n, np), kThreads, 0, s>>>(n, parent, L, xc, x);
+  });
+  return true;
+}
+
+unsigned vec_grid(size_t n) { return (unsigned)std::min<size_t>(kDotBlocks, (n + kThreads - 1) / kThreads + 1); }
+
+int cuda_fail(cdg_handle* h, cudaError_t e, const char* where) {
+  h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return CDG_ECUDA;
+}
+
+#define CDG_CHECK_LAUNCH(h, where)                        \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+template <typename T>
+const T* opA(const DevLevel& L);
+template <>
+const double* opA<double>(const DevLevel& L) { return L.A; }
+template <>
+const float* opA<float>(const DevLevel& L) { return L.A32; }
+template <typename T>
+const T* opD(const DevLevel& L);
+template <>
+const double* opD<double>(const DevLevel& L) { return L.Dinv; }
+template <>
+const float* opD<float>(const DevLevel& L) { return L.Dinv32; }
+template <typename T>
+const T* opL(const DevLevel& L);
+template <>
+const double* opL<double>(const DevLevel& L) { return L.L; }
+template <>
+const float* opL<float>(const DevLevel& L) { return L.L32; }
+
+// One V(nu_pre, nu_post) cycle from a zero guess (R14) on levels 0..n, with
+// b0 / z0 the level-0 right-hand side and result (precision T).
+template <typename T>
+bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream_t s) {
+  const int np = D.np;
+  const int nlev = D.nlev;
+  const double w = o.omega;
+  if (nlev == 1) {
+    coarse_kernel<T, T><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, b0, z0);
+    return true;
+  }
+  std::vector<const T*> bl(nlev);
+  bl[0] = b0;
+  for (int l = 1; l < nlev; ++l) bl[l] = (const T*)D.lev[l].b;
+  // downward sweep
+  for (int l = 0; l + 1 < nlev; ++l) {
+    DevLevel& L = D.lev[l];
+    T* x = (T*)L.x;
+    T* t = (T*)L.t;
+    const T* b = bl[l];
+    if (o.nu_pre >= 1) {
+      if (!launch_smooth_zero<T>(np, L.n, opD<T>(L), b, x, w, s)) return false;
+      for (int k = 1; k < o.nu_pre; ++k) {
+        if (!launch_bsr<T>(2, np, L, opA<T>(L), opD<T>(L), x, b, t, w, nullptr, s)) return false;
+        std::swap(x, t);
+      }
+      if (!launch_bsr<T>(1, np, L, opA<T>(L), nullptr, x, b, (T*)L.r, w, nullptr, s)) return false;
+      if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), (const T*)L.r,
+                              (T*)D.lev[l + 1].b, s))
+        return false;
+      // remember which buffer holds x
+      L.x = x;
+      L.t = t;
+    } else {
+      if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), b, (T*)D.lev[l + 1].b, s))
+        return false;
+    }
+  }
+  // coarsest
+  {
+    const DevLevel& C = D.lev[nlev - 1];
+    coarse_kernel<T, T><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, (const T*)C.b, (T*)C.x);
+  }
+  // upward sweep
+  for (int l = nlev - 2; l >= 0; --l) {
+    DevLevel& L = D.lev[l];
+    T* x = (T*)L.x;
+    T* t = (T*)L.t;
+    const T* b = bl[l];
+    if (!launch_prolong<T>(np, L.n, L.parent, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s))
+      return false;
+    for (int k = 0; k < o.nu_post; ++k) {
+      T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
+      if (!launch_bsr<T>(2, np, L, opA<T>(L), opD<T>(L), x, b, out, w, nullptr, s)) return false;
+      if (out == t) std::swap(x, t);
+      else x = out;
+    }
+    if (l == 0 && o.nu_post == 0)
+      cudaMemcpyAsync(z0, x, sizeof(T) * (size_t)L.n * np, cudaMemcpyDeviceToDevice, s);
+    if (l > 0) {
+      // the coarse solution of this level must sit in L.x for the next prolongation
+      if (x != (T*)L.x) {
+        L.t = L.x;
+        L.x = x;
+      }
+    }
+  }
+  return true;
+}
+
+int precond(cdg_handle* h, const double* r, double* z, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  const size_t n = (size_t)D.ndofs;
+  bool ok;
+  if (D.precision == 0) {
+    ok = vcycle<double>(D, h->opt, r, z, s);
+  } else {
+    convert_kernel<double, float><<<vec_grid(n), kThreads, 0, s>>>(n, r, D.r32);
+    ok = vcycle<float>(D, h->opt, D.r32, D.z32, s);
+    convert_kernel<float, double><<<vec_grid(n), kThreads, 0, s>>>(n, D.z32, z);
+  }
+  if (!ok) {
+    h->err = "unsupported number of basis functions per element";
+    return CDG_EINVAL;
+  }
+  CDG_CHECK_LAUNCH(h, "vcycle");
+  return CDG_OK;
+}
+
+int dot_to(cdg_handle* h, const double* x, const double* y, const double* w, int which, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  const size_t n = (size_t)D.ndofs;
+  const unsigned g = vec_grid(n);
+  dot_kernel<<<g, kThreads, 0, s>>>(n, x, y, w, D.partial, D.npartial);
+  finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)g, D.npartial, which, w != nullptr, D.scal);
+  CDG_CHECK_LAUNCH(h, "dot");
+  return CDG_OK;
+}
+
+template <typename T>
+void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  if (!src.empty()) cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s);
+}
+
+std::vector<float> to_f32(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+std::vector<int> to_i32(const std::vector<int64_t>& v) {
+  std::vector<int> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (int)v[i];
+  return o;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ entry points
+int dev_bytes(const cdg_handle* h, int64_t* bytes) {
+  *bytes = (int64_t)layout(h->H, h->opt.precision, nullptr, nullptr);
+  return CDG_OK;
+}
+
+void dev_release(cdg_handle* h) {
+  delete h->dev;
+  h->dev = nullptr;
+}
+
+int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
+  const cdg::Hierarchy& H = h->H;
+  const int64_t need = (int64_t)layout(H, h->opt.precision, nullptr, nullptr);
+  if (bytes < need) {
+    h->err = "device buffer too small: need " + std::to_string(need) + " bytes";
+    return CDG_ENOMEM;
+  }
+  if (((uintptr_t)buf & 255) != 0) {
+    h->err = "device buffer must be 256-byte aligned";
+    return CDG_EINVAL;
+  }
+  delete h->dev;
+  h->dev = new DeviceState();
+  DeviceState& D = *h->dev;
+  D.base = (char*)buf;
+  D.bytes = bytes;
+  layout(H, h->opt.precision, &D, (char*)buf);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nlev = D.nlev;
+  for (int l = 0; l < nlev; ++l) {
+    DevLevel& L = D.lev[l];
+    const cdg::BSR& A = H.A_t[l];
+    upload(L.rowptr, to_i32(A.rowptr), s);
+    upload(L.col, A.col, s);
+    if (L.A) upload(L.A, A.val, s);
+    if (L.A32) upload(L.A32, to_f32(A.val), s);
+    if (l + 1 < nlev) {
+      if (L.Dinv) upload(L.Dinv, H.Dinv_t[l], s);
+      if (L.L) upload(L.L, H.L_t[l], s);
+      if (L.Dinv32) upload(L.Dinv32, to_f32(H.Dinv_t[l]), s);
+      if (L.L32) upload(L.L32, to_f32(H.L_t[l]), s);
+      upload(L.parent, H.parent_t[l], s);
+    }
+    if (l > 0) upload(L.childptr, H.childptr_t[l], s);
+    // every synchronous upload above finishes before the host vectors die
+    cudaStreamSynchronize(s);
+  }
+  upload(D.coarse_inv, H.coarse_inv, s);
+  upload(D.rhs_vol, H.rhs_vol, s);
+  upload(D.rhs_bptr, to_i32(H.rhs_bptr), s);
+  upload(D.rhs_bface, to_i32(H.rhs_bface), s);
+  upload(D.rhs_bdata, H.rhs_bD, s);
+  upload(D.btag, std::vector<int>(H.mesh.bf_tag.begin(), H.mesh.bf_tag.end()), s);
+  upload(D.perm0, to_i32(H.order[0]), s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "bind");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "bind");
+  return CDG_OK;
+}
+
+int dev_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b, bool user_out,
+            void* stream) {
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  CDG_NP_DISPATCH(D.np, rhs_kernel<NP><<<rows_grid(D.ne, D.np), kThreads, 0, s>>>(
+                            (int)D.ne, D.nq, D.nfq, D.perm0, D.rhs_vol, f_q, D.rhs_bptr, D.rhs_bface, D.rhs_bdata,
+                            D.btag, gD, gN, b, user_out ? 1 : 0));
+  CDG_CHECK_LAUNCH(h, "rhs");
+  return CDG_OK;
+}
+
+int dev_permute(cdg_handle* h, const double* in, double* out, bool to_tree, void* stream) {
+  if (!h || !h->dev) return h ? (h->err = "not bound", CDG_ESTATE) : CDG_EINVAL;
+  DeviceState& D = *h->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  permute_kernel<<<vec_grid((size_t)D.ndofs), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, in, out, to_tree);
+  CDG_CHECK_LAUNCH(h, "permute");
+  return CDG_OK;
+}
+
+int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double* b, double* y, void* stream) {
+  if (!h) return CDG_EINVAL;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op == 5) {
+    coarse_kernel<double, double><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, x, y);
+    CDG_CHECK_LAUNCH(h, "coarse");
+    return CDG_OK;
+  }
+  if (level < 0 || level >= D.nlev || !x || !y) {
+    h->err = "bad level or NULL vector";
+    return CDG_EINVAL;
+  }
+  const DevLevel& L = D.lev[level];
+  const bool last = level + 1 == D.nlev;
+  const bool fp64 = L.A != nullptr;
+  if (((op == 2 || op == 3 || op == 4) && (last || !L.Dinv)) || (op <= 1 && !fp64) || ((op == 1 || op == 2) && !b)) {
+    h->err = "operation not available on this level in this precision";
+    return CDG_EINVAL;
+  }
+  bool ok = true;
+  if (op <= 2) ok = launch_bsr<double>(op, D.np, L, L.A, L.Dinv, x, b, y, h->opt.omega, nullptr, s);
+  else if (op == 3) ok = launch_restrict<double>(D.np, D.lev[level + 1].n, D.lev[level + 1].childptr, L.L, x, y, s);
+  else ok = launch_prolong<double>(D.np, L.n, L.parent, L.L, x, y, true, s);
+  if (!ok) {
+    h->err = "unsupported n_p";
+    return CDG_EINVAL;
+  }
+  CDG_CHECK_LAUNCH(h, "level op");
+  return CDG_OK;
+}
+
+int dev_vcycle(cdg_handle* h, const double* r, double* z, void* stream) {
+  if (!h) return CDG_EINVAL;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  return precond(h, r, z, (cudaStream_t)stream);
+}
+
+int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, const double* b_user, double* u,
+              int use_u0, double* res_hist, int* iters, int host_ptrs, void* stream) {
+  *iters = 0;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cdg_options& o = h->opt;
+  const size_t n = (size_t)D.ndofs;
+  const bool flexible = D.precision != 0;
+  double* u_dev = u;
+  int rc;
+  if (host_ptrs) {
+    cudaMemcpyAsync(D.f_stage, f_q, sizeof(double) * D.ne * D.nq, cudaMemcpyHostToDevice, s);
+    if (gD) cudaMemcpyAsync(D.gD_stage, gD, sizeof(double) * D.nbf * D.nfq, cudaMemcpyHostToDevice, s);
+    if (gN) cudaMemcpyAsync(D.gN_stage, gN, sizeof(double) * D.nbf * D.nfq, cudaMemcpyHostToDevice, s);
+    if (use_u0) cudaMemcpyAsync(D.u_stage, u, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    f_q = D.f_stage;
+    gD = gD ? D.gD_stage : nullptr;
+    gN = gN ? D.gN_stage : nullptr;
+    u_dev = D.u_stage;
+  }
+  // right-hand side in tree order
+  if (b_user) {
+    permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
+  } else if ((rc = dev_rhs(h, f_q, gD, gN, D.bt, false, s)) != CDG_OK) {
+    return rc;
+  }
+  // initial guess and residual
+  const DevLevel& L0 = D.lev[0];
+  if (use_u0) {
+    permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, u_dev, D.x, 1);
+    launch_bsr<double>(1, D.np, L0, L0.A, nullptr, D.x, D.bt, D.r, o.omega, nullptr, s);
+  } else {
+    cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
+    cudaMemcpyAsync(D.r, D.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  }
+  if ((rc = dot_to(h, D.bt, D.bt, nullptr, 3, s)) != CDG_OK) return rc;
+  if ((rc = dot_to(h, D.r, D.r, nullptr, 1, s)) != CDG_OK) return rc;
+  double hs[S_COUNT];
+  cudaMemcpyAsync(hs, D.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve init");
+  const double bnorm = std::sqrt(hs[S_BB]);
+  int status = CDG_OK;
+  int it = 0;
+  auto rel = [&](double rr) { return bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0; };
+  if (res_hist) res_hist[0] = rel(hs[S_RR]);
+  if (bnorm == 0.0) {
+    cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
+  } else if (rel(hs[S_RR]) > o.tol) {
+    if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
+    if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
+    cg_p_kernel<<<vec_grid(n), kThreads, 0, s>>>(n, D.scal, 1, D.z, D.p);
+    while (true) {
+      if (it >= o.maxit) {
+        status = CDG_ENOCONV;
+        break;
+      }
+      // q = A p and p.q
+      const unsigned g = rows_grid(L0.n, D.np);
+      launch_bsr<double>(0, D.np, L0, L0.A, nullptr, D.p, nullptr, D.q, o.omega, D.partial, s);
+      finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)g, D.npartial, 0, 0, D.scal);
+      const unsigned gv = vec_grid(n);
+      cg_update_kernel<<<gv, kThreads, 0, s>>>(n, D.scal, D.p, D.q, D.x, D.r, D.partial);
+      finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)gv, D.npartial, 1, 0, D.scal);
+      CDG_CHECK_LAUNCH(h, "cg");
+      cudaMemcpyAsync(hs, D.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cg");
+      ++it;
+      const double rr = rel(hs[S_RR]);
+      if (res_hist) res_hist[it] = rr;
+      if (!(hs[S_PQ] > 0.0) || !std::isfinite(rr)) {
+        status = CDG_EBREAKDOWN;
+        h->err = "CG breakdown: p^T A p <= 0 or non-finite residual";
+        break;
+      }
+      if (rr <= o.tol) break;
+      if (flexible) cudaMemcpyAsync(D.zold, D.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+      if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
+      if ((rc = dot_to(h, D.r, D.z, flexible ? D.zold : nullptr, 2, s)) != CDG_OK) return rc;
+      cg_p_kernel<<<vec_grid(n), kThreads, 0, s>>>(n, D.scal, 0, D.z, D.p);
+    }
+  }
+  permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, D.x, u_dev, 0);
+  if (host_ptrs) cudaMemcpyAsync(u, D.u_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve end");
+  CDG_CHECK_LAUNCH(h, "solve end");
+  *iters = it;
+  if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
+  return status;
+}

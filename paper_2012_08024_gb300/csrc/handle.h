@@ -1,0 +1,29 @@
+// Internal definition of cdg_handle shared by the host API and the device solver.
+#pragma once
+
+#include <string>
+
+#include "../../include/cdg.h"
+#include "host_setup.h"
+
+struct DeviceState;  // device.cu
+
+struct cdg_handle {
+  cdg::Hierarchy H;
+  cdg_options opt{};      // copy of the creation options (pointers cleared)
+  std::string err;
+  DeviceState* dev = nullptr;
+};
+
+// device.cu
+int dev_bytes(const cdg_handle* h, int64_t* bytes);
+int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream);
+void dev_release(cdg_handle* h);
+int dev_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b,
+            bool user_order_out, void* stream);
+int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, const double* b_user,
+              double* u, int use_u0, double* res_hist, int* iters, int host_ptrs, void* stream);
+int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double* b, double* y,
+                 void* stream);
+int dev_vcycle(cdg_handle* h, const double* r, double* z, void* stream);
+int dev_permute(cdg_handle* h, const double* in, double* out, bool to_tree, void* stream);

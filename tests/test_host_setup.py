@@ -1,0 +1,107 @@
+"""Host logic of the library against the oracle (CPU only, no device calls):
+the library's C++ set-up and the oracle share no code, so agreement pins both.
+
+* Algorithm 2 agglomeration: parents of every level bit-identical;
+* tree numbering bit-identical (children of every agglomerate contiguous);
+* A_l on every level (flux coarsening, Section 4.1) within 1e-12 relative;
+* transfer blocks L_K (Section 3.4) within 1e-12;
+* quadrature points (R3) and boundary-face order / tags identical;
+* errors: degenerate element and missing Dirichlet boundary are rejected.
+"""
+import numpy as np
+import pytest
+
+from oracle.cdg import Level0
+from oracle.hierarchy import MGHierarchy
+from synthetic import jittered_square, kuhn_cube
+from synthetic.meshes import Mesh
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2012_08024_gb300 import build
+    build.build()
+
+
+def _dense(ex, n, npb):
+    A = np.zeros((n * npb, n * npb))
+    for k in range(n):
+        for b in range(ex["rowptr"][k], ex["rowptr"][k + 1]):
+            j = ex["col"][b]
+            A[k * npb:(k + 1) * npb, j * npb:(j + 1) * npb] = ex["val"][b]
+    return A
+
+
+CASES = [
+    ("tri_p2_mixed", lambda: jittered_square(6, neumann_axes=(0,)), dict(p=2, max_levels=4)),
+    ("tri_p3", lambda: jittered_square(8), dict(p=3, max_levels=3)),
+    ("tet_p1", lambda: kuhn_cube(2), dict(p=1, max_levels=3)),
+    ("tet_p2_seed", lambda: kuhn_cube(2, seed=4), dict(p=2, max_levels=3, seed=11)),
+    ("tri_natural", lambda: jittered_square(5), dict(p=1, max_levels=3, switch_kind=1)),
+    ("tri_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3,
+                                                  kappa=np.exp(np.random.default_rng(1).standard_normal(50)))),
+]
+
+
+@pytest.mark.parametrize("name,mk,kw", CASES, ids=[c[0] for c in CASES])
+def test_library_setup_matches_oracle(name, mk, kw):
+    from paper_2012_08024_gb300 import Solver
+    mesh = mk()
+    S = Solver(mesh, **kw)
+    okw = dict(p=kw["p"], switch_kind=kw.get("switch_kind", 0), kappa=kw.get("kappa"))
+    L0 = Level0(mesh, **okw)
+    H = MGHierarchy(L0, max_levels=kw["max_levels"], seed=kw.get("seed", 0))
+    assert S.n_levels == H.n_levels
+    order = H.agg.tree_order()
+    npb = L0.np_
+    for l in range(H.n_levels - 1):
+        assert list(S.export_agglomeration(l)) == H.agg.parent[l]
+    for l in range(H.n_levels):
+        ex = S.export_level(l)
+        assert list(ex["perm"]) == order[l]
+        n = len(order[l])
+        P = np.zeros((n * npb, n * npb))
+        for k, w in enumerate(order[l]):
+            P[k * npb:(k + 1) * npb, w * npb:(w + 1) * npb] = np.eye(npb)
+        Aor = P @ H.A[l].toarray() @ P.T
+        Alib = _dense(ex, n, npb)
+        assert np.abs(Alib - Aor).max() <= 1e-12 * np.abs(Aor).max()
+        if l + 1 < H.n_levels:
+            Lor = np.array([H.Lblk[l][w] for w in order[l]])
+            assert np.abs(ex["L"] - Lor).max() <= 1e-12
+            pos = {w: k for k, w in enumerate(order[l + 1])}
+            assert list(ex["parent"]) == [pos[H.agg.parent[l][w]] for w in order[l]]
+    xq, xbq, btag = S.quadrature_points()
+    assert np.abs(xq - L0.all_volume_points()).max() < 1e-14
+    assert np.abs(xbq - L0.all_boundary_points()).max() < 1e-14
+    assert list(btag) == [t for (_, _, t) in L0.topo.boundary]
+    assert abs(S.info["C_D"] - L0.C_D) <= 1e-12 * L0.C_D
+
+
+def test_agglomeration_bit_exact_larger_mesh():
+    from paper_2012_08024_gb300 import Solver
+    from oracle.agglomerate import Hierarchy
+    from oracle.mesh import Topology
+    mesh = jittered_square(40, seed=3)
+    S = Solver(mesh, p=1, max_levels=6, seed=5)
+    t = Topology(mesh)
+    Ho = Hierarchy([list(map(int, e)) for e in mesh.elem], t.nbrs, 6, 5)
+    for l in range(Ho.n_levels - 1):
+        assert list(S.export_agglomeration(l)) == Ho.parent[l]
+
+
+def test_errors_are_reported():
+    from paper_2012_08024_gb300 import CdgError, Solver
+    m = jittered_square(2)
+    bad = Mesh(2, m.xyz.copy(), m.elem.copy(), m.bface, m.btag)
+    bad.elem[0] = [0, 1, 2]        # collinear vertices 0, 1, 2 on y = 0
+    with pytest.raises(CdgError) as e:
+        Solver(bad, p=1)
+    assert e.value.code == 2
+    allneu = Mesh(2, m.xyz, m.elem, m.bface, np.ones(len(m.btag), dtype=np.int32))
+    with pytest.raises(CdgError) as e:
+        Solver(allneu, p=1)
+    assert e.value.code == 2 and "Dirichlet" in str(e.value)
+    with pytest.raises(CdgError) as e:
+        Solver(m, p=0)
+    assert e.value.code == 1
