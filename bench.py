@@ -1,0 +1,324 @@
+"""Benchmark of the solve phase: V-cycle preconditioned CG on the CDG Poisson
+operator of a 512 x 512 jittered square (524,288 triangles, p = 3, 5.24M
+dofs, 7 agglomeration levels, V(2,2), FP64, relative residual 1e-10).
+
+One step = one complete solve from f sampled at the quadrature points (device
+resident) to the DG coefficients u (device), i.e. right-hand-side assembly +
+PCG iterations to 1e-10.  value = solved DOF/s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload tri512_p3|tri256_p3|tri32_p2|tet48_p2]
+
+Under torchrun (N > 1) every rank solves its own copy (replicas, weak scaling);
+the timed region is bracketed by barriers and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import os
+
+# the CPU-baseline legs time the single-threaded oracle: keep numpy's BLAS on one core
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, n, p, levels, nu, precision)
+    "tri512_p3": ("square", 512, 3, 7, 2, "fp64"),
+    "tri256_p3": ("square", 256, 3, 6, 2, "fp64"),
+    "tri32_p2": ("square", 32, 2, 4, 1, "fp64"),
+    "tet48_p2": ("cube", 48, 2, 6, 1, "fp32"),
+}
+METRIC = "solved DOF/s (PCG+V-cycle to 1e-10)"
+HBM_FALLBACK_GBS = 6800.0           # profiling-recipe fallback when no measured peak file exists
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal)
+
+
+def make_mesh(kind, n):
+    from synthetic import jittered_square, kuhn_cube
+    return jittered_square(n) if kind == "square" else kuhn_cube(n)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(kind, p, nu, seconds_target=10.0):
+    """Oracle (plain FP64 numpy/scipy) on a bounded sample of the workload: the
+    same generator and discretisation on a 64 x 64 square (8,192 triangles) or
+    a 12^3 cube, oracle set-up untimed, its PCG + V-cycle solve timed."""
+    from oracle.cdg import Level0
+    from oracle.hierarchy import MGHierarchy
+    from oracle.solver import VCycle, pcg
+    from synthetic import sin_source
+    n = 64 if kind == "square" else 12
+    mesh = make_mesh(kind, n)
+    L0 = Level0(mesh, p)
+    H = MGHierarchy(L0, max_levels=5)
+    V = VCycle(H.A, H.L, L0.np_, nu, nu)
+    b = L0.rhs(sin_source(L0.all_volume_points()))
+    times, its = [], []
+    t_end = time.perf_counter() + seconds_target
+    while True:
+        t0 = time.perf_counter()
+        x, hist, it = pcg(H.A[0], b, V.apply, tol=1e-10)
+        times.append(time.perf_counter() - t0)
+        its.append(it)
+        if time.perf_counter() > t_end or len(times) >= 50:
+            break
+    ndof = H.A[0].shape[0]
+    return {"value": ndof / statistics.median(times), "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{'square' if kind == 'square' else 'cube'} n={n} ({mesh.n_elements} elements, "
+                      f"{ndof} dofs), p={p}, {H.n_levels} levels, V({nu},{nu}), tol 1e-10, "
+                      f"{its[0]} iterations, median of {len(times)} solves, set-up untimed"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    kind, n, p, lv, nu, prec = WORKLOADS[args.workload]
+    from oracle.cdg import Level0
+    from oracle.hierarchy import MGHierarchy
+    from oracle.solver import VCycle, pcg
+    from synthetic import sin_source
+    ns = 64 if kind == "square" else 12
+    mesh = make_mesh(kind, ns)
+    L0 = Level0(mesh, p)
+    H = MGHierarchy(L0, max_levels=5)
+    V = VCycle(H.A, H.L, L0.np_, nu, nu)
+    fq = sin_source(L0.all_volume_points())
+    for _ in range(args.warmup):
+        pcg(H.A[0], L0.rhs(fq), V.apply, tol=1e-10)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b = L0.rhs(fq)
+        x, hist, it = pcg(H.A[0], b, V.apply, tol=1e-10)
+    dt = (time.perf_counter() - t0) / args.steps
+    ndof = H.A[0].shape[0]
+    val = ndof / dt
+    sample = (f"oracle on a {ns}^{2 if kind == 'square' else 3} {'square' if kind == 'square' else 'cube'} sample "
+              f"({mesh.n_elements} elements, {ndof} dofs), p={p}, V({nu},{nu}), each step = rhs + PCG to 1e-10")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tri512_p3", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2012_08024_gb300 as pkg
+    from synthetic import sin_source
+    kind, n, p, lv, nu, prec = WORKLOADS[args.workload]
+    mesh = make_mesh(kind, n)
+    t0 = time.perf_counter()
+    S = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10, maxit=500)
+    setup_s = time.perf_counter() - t0
+    S.bind(dev)
+    xq, _, _ = S.quadrature_points()
+    fq_host = sin_source(xq)
+    fq = torch.tensor(fq_host, device=dev)
+    ndof = S.info["n_dofs"]
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident solves
+    for _ in range(max(args.warmup, 3)):
+        u, hist, it, rc = S.solve(fq)
+    barrier()
+    l0 = pkg.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    with ClockSampler(dev.index) as cs:
+        e0.record(stream)
+        for _ in range(args.steps):
+            u, hist, it, rc = S.solve(fq)
+            iters.append(it)
+        e1.record(stream)
+        barrier()
+    launches = pkg.kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ndof * ws / (ms * 1e-3)
+    # ---- end to end through the C ABI with pinned host buffers
+    fq_pin = torch.tensor(fq_host).pin_memory()
+    u_pin = torch.empty((S.ne, S.np_), dtype=torch.float64).pin_memory()
+    import ctypes as C
+    hist_h = np.zeros(S.maxit + 1)
+    itc = C.c_int32(0)
+
+    def solve_host():
+        return pkg.lib().cdg_solve(S._h, fq_pin.data_ptr(), None, None, u_pin.data_ptr(), 0,
+                                   hist_h.ctypes.data, C.byref(itc), 1, stream.cuda_stream)
+    for _ in range(2):
+        solve_host()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        solve_host()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    # ---- dominant kernel: level-0 FP64 block-sparse apply, timed on the launching stream
+    x0 = torch.randn(ndof, dtype=torch.float64, device=dev)
+    y0 = torch.empty_like(x0)
+    for _ in range(3):
+        S.apply(0, x0, y0)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        S.apply(0, x0, y0)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    k_us = e0.elapsed_time(e1) / reps * 1e3
+    nnzb0 = S.info["nnzb_l"][0]
+    npb = S.np_
+    alg_bytes = nnzb0 * npb * npb * 8 + nnzb0 * 4 + (S.ne + 1) * 4 + 2 * ndof * 8
+    achieved = alg_bytes / (k_us * 1e-6) / 1e9
+    peak, peak_src = peaks()
+    flops = 2.0 * nnzb0 * npb * npb
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(kind, p, nu)
+    clocks = cs.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "mesh": f"{kind} {n}", "elements": S.ne, "p": p, "dofs": ndof,
+                   "levels": S.n_levels, "n_l": S.info["n_l"], "nnzb_l": S.info["nnzb_l"],
+                   "smoother": f"V({nu},{nu}) block Jacobi omega=2/3", "tol": 1e-10, "precision": prec,
+                   "iterations": iters[-1], "setup_s": round(setup_s, 3), "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (operator %.2f GB)" % (S.info["device_bytes"] / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0>)" % npb,
+                     "alg_bytes_per_launch": alg_bytes, "launch_us": k_us,
+                     "fp64_tflops": flops / (k_us * 1e-6) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS},
+        "e2e": {"value": ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
+                "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
