@@ -76,6 +76,7 @@ SIGNATURES = {
     "cdg_vcycle": (_I32, [_P, _P, _P, _P]),
     "cdg_to_tree": (_I32, [_P, _P, _P, _P]),
     "cdg_to_user": (_I32, [_P, _P, _P, _P]),
+    "cdg_kernel_launches": (_I64, []),
 }
 
 
@@ -92,6 +93,11 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().cdg_kernel_launches())
 
 
 def _ptr(a) -> int | None:

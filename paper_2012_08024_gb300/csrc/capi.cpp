@@ -284,4 +284,6 @@ int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream) {
   return dev_permute(h, tree, user, false, stream);
 }
 
+int64_t cdg_kernel_launches(void) { return (int64_t)dev_launch_count(); }
+
 }  // extern "C"

@@ -18,6 +18,10 @@
 
 #include "handle.h"
 
+#include <atomic>
+
+static std::atomic<long long> g_launches{0};
+
 namespace {
 
 constexpr int kMaxLev = CDG_MAX_LEVELS;
@@ -39,6 +43,12 @@ struct DevLevel {
   float* A32 = nullptr;
   float* Dinv32 = nullptr;
   float* L32 = nullptr;
+  int* hrowptr = nullptr;    // Ahat = D^{-1}(A - D): row-scaled off-diagonal blocks (smoother)
+  int* hcol = nullptr;
+  double* Ahat = nullptr;
+  float* Ahat32 = nullptr;
+  int64_t hnnzb = 0;
+  void* bh = nullptr;        // D^{-1} b of the current V-cycle visit
   void* x = nullptr;         // V-cycle work vectors in the V-cycle precision
   void* t = nullptr;
   void* r = nullptr;
@@ -120,13 +130,19 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
     // FP64 operator: level 0 always (outer CG); all levels in FP64 mode
     if (l == 0 || precision == 0) L.A = c.take<double>(A.val.size());
     if (!last) {
+      const cdg::BSR& Sh = H.Ahat_t[l];
+      L.hnnzb = Sh.nnzb();
+      L.hrowptr = c.take<int>(Sh.nrows + 1);
+      L.hcol = c.take<int>(Sh.nnzb() + 1);
       if (precision == 0) {
         L.Dinv = c.take<double>((size_t)L.n * nb2);
         L.L = c.take<double>((size_t)L.n * nb2);
+        L.Ahat = c.take<double>(Sh.val.size() + 1);
       } else {
         L.A32 = c.take<float>(A.val.size());
         L.Dinv32 = c.take<float>((size_t)L.n * nb2);
         L.L32 = c.take<float>((size_t)L.n * nb2);
+        L.Ahat32 = c.take<float>(Sh.val.size() + 1);
       }
       L.parent = c.take<int>(L.n);
     }
@@ -136,6 +152,7 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
     L.t = c.take<char>(nv * vsz);
     L.r = c.take<char>(nv * vsz);
     L.b = c.take<char>(nv * vsz);
+    L.bh = c.take<char>(nv * (l == 0 ? sizeof(double) : vsz));
   }
   D.nc = (int)(H.lev.back().n * np);
   D.coarse_inv = c.take<double>((size_t)D.nc * D.nc);
@@ -174,8 +191,9 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
 // One thread per scalar row: lane = sub * NP + i handles row i of block row
 // warp * (32 / NP) + sub.  MODE 0: y = A x, 1: y = b - A x,
-// 2: y = x + omega Dinv (b - A x).  With dot != nullptr, MODE 0 also writes the
-// block partial of sum_i x_i y_i (for p^T A p).
+// 3: y = x + omega (bh - x - Ahat x) with Ahat = D^{-1}(A - D) and bh = D^{-1} b,
+// i.e. one damped block-Jacobi step.  With dot != nullptr, MODE 0 also writes
+// the block partial of sum_i x_i y_i (for p^T A p).
 template <typename T, int NP, int MODE>
 __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restrict__ rowptr,
                                                        const int* __restrict__ col, const T* __restrict__ A,
@@ -215,28 +233,17 @@ __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restr
         dot[blockIdx.x] = s;
       }
     }
-  } else {
-    const T r = active ? b[row] - acc : T(0);
-    if (MODE == 1) {
-      if (active) y[row] = r;
-    } else {
-      T s = T(0);
-      const T* D = Dinv + (size_t)(active ? K : 0) * NP * NP + i * NP;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const T rj = __shfl_sync(0xffffffffu, r, sub * NP + j);
-        if (active) s = fma(ldg(D + j), rj, s);
-      }
-      if (active) y[row] = x[row] + omega * s;
-    }
+  } else if (active) {
+    if (MODE == 1) y[row] = b[row] - acc;
+    else y[row] = x[row] + omega * (b[row] - x[row] - acc);
   }
 }
 
-// x = omega Dinv b (first smoothing step from a zero guess)
-template <typename T, int NP>
-__global__ void __launch_bounds__(kThreads) smooth_zero_kernel(int n, const T* __restrict__ Dinv,
-                                                               const T* __restrict__ b, T* __restrict__ x,
-                                                               T omega) {
+// bh = Dinv b; with WRITE_X also x = omega bh (first smoothing step from a zero guess)
+template <typename T, int NP, bool WRITE_X>
+__global__ void __launch_bounds__(kThreads) smooth_first_kernel(int n, const T* __restrict__ Dinv,
+                                                                const T* __restrict__ b, T* __restrict__ bh,
+                                                                T* __restrict__ x, T omega) {
   constexpr int RPW = 32 / NP;
   const int lane = threadIdx.x & 31;
   const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -249,7 +256,8 @@ __global__ void __launch_bounds__(kThreads) smooth_zero_kernel(int n, const T* _
   T s = T(0);
 #pragma unroll
   for (int j = 0; j < NP; ++j) s = fma(ldg(D + j), ldg(bk + j), s);
-  x[(size_t)K * NP + i] = omega * s;
+  bh[(size_t)K * NP + i] = s;
+  if (WRITE_X) x[(size_t)K * NP + i] = omega * s;
 }
 
 // bc[A] = sum over children K of L_K^T r[K]
@@ -295,15 +303,18 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(int n, const int* __r
   x[row] = ADD ? x[row] + s : s;
 }
 
-// dense symmetric inverse times vector: x[i] = sum_j Ainv[j][i] b[j] (FP64)
+// dense symmetric inverse times vector, one warp per row: x[i] = sum_j Ainv[i][j] b[j] (FP64)
 template <typename TI, typename TO>
 __global__ void coarse_kernel(int nc, const double* __restrict__ Ainv, const TI* __restrict__ b,
                               TO* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc) return;
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nc) return;
+  const double* a = Ainv + (size_t)row * nc;
   double s = 0.0;
-  for (int j = 0; j < nc; ++j) s = fma(Ainv[(size_t)j * nc + i], (double)b[j], s);
-  x[i] = (TO)s;
+  for (int j = lane; j < nc; j += 32) s = fma(a[j], (double)b[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = (TO)s;
 }
 
 template <typename TI, typename TO>
@@ -447,6 +458,14 @@ __global__ void permute_kernel(int ne, int np, const int* __restrict__ perm0, co
 }
 
 // ------------------------------------------------------------------ launch helpers
+// Every kernel launch of the library goes through here (counted for the
+// benchmark's launch accounting).
+template <typename... KArgs, typename... Args>
+inline void launch(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+  k<<<g, b, 0, s>>>(args...);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 inline unsigned rows_grid(int64_t nrows, int np) {
   const int64_t rpw = 32 / np;
   const int64_t warps = (nrows + rpw - 1) / rpw;
@@ -466,38 +485,44 @@ inline unsigned rows_grid(int64_t nrows, int np) {
     default: return false;                                 \
   }
 
+// mode 0: y = A x (+ dot partials), 1: y = b - A x, 3: y = x + omega (bh - x - Ahat x)
 template <typename T>
-bool launch_bsr(int mode, int np, const DevLevel& L, const T* A, const T* Dinv, const T* x, const T* b, T* y,
-                double omega, double* dot, cudaStream_t s) {
-  const unsigned g = rows_grid(L.n, np);
+bool launch_bsr(int mode, int np, int n, const int* rowptr, const int* col, const T* A, const T* x, const T* b,
+                T* y, double omega, double* dot, cudaStream_t s) {
+  const unsigned g = rows_grid(n, np);
   CDG_NP_DISPATCH(np, {
     if (mode == 0)
-      bsr_kernel<T, NP, 0><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, dot);
+      launch(bsr_kernel<T, NP, 0>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega, dot);
     else if (mode == 1)
-      bsr_kernel<T, NP, 1><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, nullptr);
+      launch(bsr_kernel<T, NP, 1>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
+             (double*)nullptr);
     else
-      bsr_kernel<T, NP, 2><<<g, kThreads, 0, s>>>(L.n, L.rowptr, L.col, A, Dinv, x, b, y, (T)omega, nullptr);
+      launch(bsr_kernel<T, NP, 3>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
+             (double*)nullptr);
   });
   return true;
 }
 
 template <typename T>
-bool launch_smooth_zero(int np, int n, const T* Dinv, const T* b, T* x, double omega, cudaStream_t s) {
-  CDG_NP_DISPATCH(np, smooth_zero_kernel<T, NP><<<rows_grid(n, np), kThreads, 0, s>>>(n, Dinv, b, x, (T)omega));
+bool launch_smooth_first(int np, int n, const T* Dinv, const T* b, T* bh, T* x, double omega, cudaStream_t s) {
+  CDG_NP_DISPATCH(np, {
+    if (x) launch(smooth_first_kernel<T, NP, true>, rows_grid(n, np), kThreads, s, n, Dinv, b, bh, x, (T)omega);
+    else launch(smooth_first_kernel<T, NP, false>, rows_grid(n, np), kThreads, s, n, Dinv, b, bh, x, (T)omega);
+  });
   return true;
 }
 
 template <typename T>
 bool launch_restrict(int np, int nc, const int* cp, const T* L, const T* r, T* bc, cudaStream_t s) {
-  CDG_NP_DISPATCH(np, restrict_kernel<T, NP><<<rows_grid(nc, np), kThreads, 0, s>>>(nc, cp, L, r, bc));
+  CDG_NP_DISPATCH(np, launch(restrict_kernel<T, NP>, rows_grid(nc, np), kThreads, s, nc, cp, L, r, bc));
   return true;
 }
 
 template <typename T>
 bool launch_prolong(int np, int n, const int* parent, const T* L, const T* xc, T* x, bool add, cudaStream_t s) {
   CDG_NP_DISPATCH(np, {
-    if (add) prolong_kernel<T, NP, true><<<rows_grid(n, np), kThreads, 0, s>>>(n, parent, L, xc, x);
-    else prolong_kernel<T, NP, false><<<rows_grid(n, np), kThreads, 0, s>>>(n, parent, L, xc, x);
+    if (add) launch(prolong_kernel<T, NP, true>, rows_grid(n, np), kThreads, s, n, parent, L, xc, x);
+    else launch(prolong_kernel<T, NP, false>, rows_grid(n, np), kThreads, s, n, parent, L, xc, x);
   });
   return true;
 }
@@ -528,6 +553,12 @@ const double* opD<double>(const DevLevel& L) { return L.Dinv; }
 template <>
 const float* opD<float>(const DevLevel& L) { return L.Dinv32; }
 template <typename T>
+const T* opH(const DevLevel& L);
+template <>
+const double* opH<double>(const DevLevel& L) { return L.Ahat; }
+template <>
+const float* opH<float>(const DevLevel& L) { return L.Ahat32; }
+template <typename T>
 const T* opL(const DevLevel& L);
 template <>
 const double* opL<double>(const DevLevel& L) { return L.L; }
@@ -542,7 +573,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   const int nlev = D.nlev;
   const double w = o.omega;
   if (nlev == 1) {
-    coarse_kernel<T, T><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, b0, z0);
+    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, b0, z0);
     return true;
   }
   std::vector<const T*> bl(nlev);
@@ -554,13 +585,14 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     T* x = (T*)L.x;
     T* t = (T*)L.t;
     const T* b = bl[l];
+    T* bh = (T*)L.bh;
     if (o.nu_pre >= 1) {
-      if (!launch_smooth_zero<T>(np, L.n, opD<T>(L), b, x, w, s)) return false;
+      if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, x, w, s)) return false;
       for (int k = 1; k < o.nu_pre; ++k) {
-        if (!launch_bsr<T>(2, np, L, opA<T>(L), opD<T>(L), x, b, t, w, nullptr, s)) return false;
+        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s)) return false;
         std::swap(x, t);
       }
-      if (!launch_bsr<T>(1, np, L, opA<T>(L), nullptr, x, b, (T*)L.r, w, nullptr, s)) return false;
+      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s)) return false;
       if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), (const T*)L.r,
                               (T*)D.lev[l + 1].b, s))
         return false;
@@ -568,6 +600,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
       L.x = x;
       L.t = t;
     } else {
+      if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, (T*)nullptr, w, s)) return false;
       if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), b, (T*)D.lev[l + 1].b, s))
         return false;
     }
@@ -575,19 +608,19 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   // coarsest
   {
     const DevLevel& C = D.lev[nlev - 1];
-    coarse_kernel<T, T><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, (const T*)C.b, (T*)C.x);
+    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, (const T*)C.b, (T*)C.x);
   }
   // upward sweep
   for (int l = nlev - 2; l >= 0; --l) {
     DevLevel& L = D.lev[l];
     T* x = (T*)L.x;
     T* t = (T*)L.t;
-    const T* b = bl[l];
     if (!launch_prolong<T>(np, L.n, L.parent, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s))
       return false;
     for (int k = 0; k < o.nu_post; ++k) {
       T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
-      if (!launch_bsr<T>(2, np, L, opA<T>(L), opD<T>(L), x, b, out, w, nullptr, s)) return false;
+      if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s))
+        return false;
       if (out == t) std::swap(x, t);
       else x = out;
     }
@@ -611,9 +644,9 @@ int precond(cdg_handle* h, const double* r, double* z, cudaStream_t s) {
   if (D.precision == 0) {
     ok = vcycle<double>(D, h->opt, r, z, s);
   } else {
-    convert_kernel<double, float><<<vec_grid(n), kThreads, 0, s>>>(n, r, D.r32);
+    launch(convert_kernel<double, float>, vec_grid(n), kThreads, s, n, r, D.r32);
     ok = vcycle<float>(D, h->opt, D.r32, D.z32, s);
-    convert_kernel<float, double><<<vec_grid(n), kThreads, 0, s>>>(n, D.z32, z);
+    launch(convert_kernel<float, double>, vec_grid(n), kThreads, s, n, D.z32, z);
   }
   if (!ok) {
     h->err = "unsupported number of basis functions per element";
@@ -627,8 +660,8 @@ int dot_to(cdg_handle* h, const double* x, const double* y, const double* w, int
   DeviceState& D = *h->dev;
   const size_t n = (size_t)D.ndofs;
   const unsigned g = vec_grid(n);
-  dot_kernel<<<g, kThreads, 0, s>>>(n, x, y, w, D.partial, D.npartial);
-  finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)g, D.npartial, which, w != nullptr, D.scal);
+  launch(dot_kernel, g, kThreads, s, n, x, y, w, D.partial, D.npartial);
+  launch(finalize_kernel, 1, kThreads, s, D.partial, (int)g, D.npartial, which, w != nullptr, D.scal);
   CDG_CHECK_LAUNCH(h, "dot");
   return CDG_OK;
 }
@@ -653,6 +686,8 @@ std::vector<int> to_i32(const std::vector<int64_t>& v) {
 }  // namespace
 
 // ------------------------------------------------------------------ entry points
+long long dev_launch_count() { return g_launches.load(); }
+
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
   *bytes = (int64_t)layout(h->H, h->opt.precision, nullptr, nullptr);
   return CDG_OK;
@@ -695,6 +730,11 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
       if (L.Dinv32) upload(L.Dinv32, to_f32(H.Dinv_t[l]), s);
       if (L.L32) upload(L.L32, to_f32(H.L_t[l]), s);
       upload(L.parent, H.parent_t[l], s);
+      const cdg::BSR& Sh = H.Ahat_t[l];
+      upload(L.hrowptr, to_i32(Sh.rowptr), s);
+      upload(L.hcol, Sh.col, s);
+      if (L.Ahat) upload(L.Ahat, Sh.val, s);
+      if (L.Ahat32) upload(L.Ahat32, to_f32(Sh.val), s);
     }
     if (l > 0) upload(L.childptr, H.childptr_t[l], s);
     // every synchronous upload above finishes before the host vectors die
@@ -722,7 +762,7 @@ int dev_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN
   }
   DeviceState& D = *h->dev;
   cudaStream_t s = (cudaStream_t)stream;
-  CDG_NP_DISPATCH(D.np, rhs_kernel<NP><<<rows_grid(D.ne, D.np), kThreads, 0, s>>>(
+  CDG_NP_DISPATCH(D.np, launch(rhs_kernel<NP>, rows_grid(D.ne, D.np), kThreads, s, 
                             (int)D.ne, D.nq, D.nfq, D.perm0, D.rhs_vol, f_q, D.rhs_bptr, D.rhs_bface, D.rhs_bdata,
                             D.btag, gD, gN, b, user_out ? 1 : 0));
   CDG_CHECK_LAUNCH(h, "rhs");
@@ -733,7 +773,7 @@ int dev_permute(cdg_handle* h, const double* in, double* out, bool to_tree, void
   if (!h || !h->dev) return h ? (h->err = "not bound", CDG_ESTATE) : CDG_EINVAL;
   DeviceState& D = *h->dev;
   cudaStream_t s = (cudaStream_t)stream;
-  permute_kernel<<<vec_grid((size_t)D.ndofs), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, in, out, to_tree);
+  launch(permute_kernel, vec_grid((size_t)D.ndofs), kThreads, s, (int)D.ne, D.np, D.perm0, in, out, to_tree);
   CDG_CHECK_LAUNCH(h, "permute");
   return CDG_OK;
 }
@@ -747,7 +787,7 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   DeviceState& D = *h->dev;
   cudaStream_t s = (cudaStream_t)stream;
   if (op == 5) {
-    coarse_kernel<double, double><<<(D.nc + 127) / 128, 128, 0, s>>>(D.nc, D.coarse_inv, x, y);
+    launch(coarse_kernel<double, double>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, x, y);
     CDG_CHECK_LAUNCH(h, "coarse");
     return CDG_OK;
   }
@@ -763,7 +803,13 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
     return CDG_EINVAL;
   }
   bool ok = true;
-  if (op <= 2) ok = launch_bsr<double>(op, D.np, L, L.A, L.Dinv, x, b, y, h->opt.omega, nullptr, s);
+  if (op <= 1) {
+    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s);
+  } else if (op == 2) {
+    ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, (double*)L.bh, (double*)nullptr, h->opt.omega, s) &&
+         launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)L.bh, y, h->opt.omega,
+                            nullptr, s);
+  }
   else if (op == 3) ok = launch_restrict<double>(D.np, D.lev[level + 1].n, D.lev[level + 1].childptr, L.L, x, y, s);
   else ok = launch_prolong<double>(D.np, L.n, L.parent, L.L, x, y, true, s);
   if (!ok) {
@@ -809,15 +855,15 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   }
   // right-hand side in tree order
   if (b_user) {
-    permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
+    launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
   } else if ((rc = dev_rhs(h, f_q, gD, gN, D.bt, false, s)) != CDG_OK) {
     return rc;
   }
   // initial guess and residual
   const DevLevel& L0 = D.lev[0];
   if (use_u0) {
-    permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, u_dev, D.x, 1);
-    launch_bsr<double>(1, D.np, L0, L0.A, nullptr, D.x, D.bt, D.r, o.omega, nullptr, s);
+    launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, u_dev, D.x, 1);
+    launch_bsr<double>(1, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.x, D.bt, D.r, o.omega, nullptr, s);
   } else {
     cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
     cudaMemcpyAsync(D.r, D.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
@@ -838,7 +884,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   } else if (rel(hs[S_RR]) > o.tol) {
     if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
     if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
-    cg_p_kernel<<<vec_grid(n), kThreads, 0, s>>>(n, D.scal, 1, D.z, D.p);
+    launch(cg_p_kernel, vec_grid(n), kThreads, s, n, D.scal, 1, D.z, D.p);
     while (true) {
       if (it >= o.maxit) {
         status = CDG_ENOCONV;
@@ -846,11 +892,12 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
       }
       // q = A p and p.q
       const unsigned g = rows_grid(L0.n, D.np);
-      launch_bsr<double>(0, D.np, L0, L0.A, nullptr, D.p, nullptr, D.q, o.omega, D.partial, s);
-      finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)g, D.npartial, 0, 0, D.scal);
+      launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, o.omega,
+                         D.partial, s);
+      launch(finalize_kernel, 1, kThreads, s, D.partial, (int)g, D.npartial, 0, 0, D.scal);
       const unsigned gv = vec_grid(n);
-      cg_update_kernel<<<gv, kThreads, 0, s>>>(n, D.scal, D.p, D.q, D.x, D.r, D.partial);
-      finalize_kernel<<<1, kThreads, 0, s>>>(D.partial, (int)gv, D.npartial, 1, 0, D.scal);
+      launch(cg_update_kernel, gv, kThreads, s, n, D.scal, D.p, D.q, D.x, D.r, D.partial);
+      launch(finalize_kernel, 1, kThreads, s, D.partial, (int)gv, D.npartial, 1, 0, D.scal);
       CDG_CHECK_LAUNCH(h, "cg");
       cudaMemcpyAsync(hs, D.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
@@ -867,10 +914,10 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
       if (flexible) cudaMemcpyAsync(D.zold, D.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
       if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
       if ((rc = dot_to(h, D.r, D.z, flexible ? D.zold : nullptr, 2, s)) != CDG_OK) return rc;
-      cg_p_kernel<<<vec_grid(n), kThreads, 0, s>>>(n, D.scal, 0, D.z, D.p);
+      launch(cg_p_kernel, vec_grid(n), kThreads, s, n, D.scal, 0, D.z, D.p);
     }
   }
-  permute_kernel<<<vec_grid(n), kThreads, 0, s>>>((int)D.ne, D.np, D.perm0, D.x, u_dev, 0);
+  launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, D.x, u_dev, 0);
   if (host_ptrs) cudaMemcpyAsync(u, D.u_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve end");

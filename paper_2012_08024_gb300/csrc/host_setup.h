@@ -115,6 +115,7 @@ struct Hierarchy {
   // level data in tree order (what the device uses)
   std::vector<BSR> A_t;                       // per level
   std::vector<std::vector<double>> Dinv_t;    // per level except coarsest: [n][np][np]
+  std::vector<BSR> Ahat_t;                    // per level except coarsest: D^{-1} A without the diagonal blocks
   std::vector<std::vector<double>> L_t;       // per level except coarsest
   std::vector<std::vector<i32>> parent_t;     // per level except coarsest
   std::vector<std::vector<i32>> childptr_t;   // per level except finest: [n+1]
@@ -151,5 +152,6 @@ std::vector<std::vector<i64>> greedy_agglomerate(const std::vector<std::vector<i
 bool cholesky(int n, double* a);                  // in place, lower; false if not SPD
 void lower_inverse(int n, const double* l, double* inv);
 bool spd_inverse(int n, const double* a, double* inv);
+bool lu_inverse(int n, const double* a, double* inv);    // partial pivoting; false if singular
 
 }  // namespace cdg

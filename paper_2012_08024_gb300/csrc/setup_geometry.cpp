@@ -163,6 +163,41 @@ void lower_inverse(int n, const double* l, double* inv) {
   }
 }
 
+// Gauss-Jordan inverse with partial pivoting; false if singular to working precision.
+bool lu_inverse(int n, const double* a, double* inv) {
+  std::vector<double> m(a, a + (size_t)n * n);
+  std::fill(inv, inv + (size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  double scale = 0.0;
+  for (size_t t = 0; t < (size_t)n * n; ++t) scale = std::max(scale, std::fabs(a[t]));
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(m[(size_t)r * n + c]) > std::fabs(m[(size_t)piv * n + c])) piv = r;
+    if (!(std::fabs(m[(size_t)piv * n + c]) > 1e-14 * scale)) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(m[(size_t)piv * n + k], m[(size_t)c * n + k]);
+        std::swap(inv[(size_t)piv * n + k], inv[(size_t)c * n + k]);
+      }
+    const double d = 1.0 / m[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      m[(size_t)c * n + k] *= d;
+      inv[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = m[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        m[(size_t)r * n + k] -= f * m[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  return true;
+}
+
 bool spd_inverse(int n, const double* a, double* inv) {
   std::vector<double> l(a, a + (size_t)n * n), li((size_t)n * n);
   if (!cholesky(n, l.data())) return false;

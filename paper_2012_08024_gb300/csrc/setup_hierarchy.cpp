@@ -6,6 +6,7 @@
 #include <cstring>
 #include <queue>
 #include <stdexcept>
+#include <string>
 
 #include "host_setup.h"
 
@@ -418,6 +419,7 @@ void finalize_tree_order(Hierarchy& H) {
   const size_t nb2 = (size_t)np * np;
   H.A_t.assign(nlev, BSR());
   H.Dinv_t.assign(nlev, {});
+  H.Ahat_t.assign(nlev, BSR());
   H.L_t.assign(nlev, {});
   H.parent_t.assign(nlev, {});
   H.childptr_t.assign(nlev, {});
@@ -447,11 +449,44 @@ void finalize_tree_order(Hierarchy& H) {
         T.col[T.rowptr[k] + t] = cb[t].first;
         std::memcpy(T.block(T.rowptr[k] + t), A.block(cb[t].second), nb2 * sizeof(double));
         if (cb[t].first == k && l + 1 < nlev) {
-          if (!spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2])) notspd = true;
+          // flux-coarsened operators need not be definite (observed on 3D meshes):
+          // fall back to a pivoted inverse when the Cholesky factorisation fails
+          if (!spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]) &&
+              !lu_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]))
+            notspd = true;
         }
       }
     }
-    if (notspd) throw std::runtime_error("diagonal block not positive definite");
+    if (notspd) throw std::runtime_error("singular diagonal block on level " + std::to_string(l));
+    if (l + 1 < nlev) {
+      // row-scaled off-diagonal operator Ahat = D^{-1} (A - D) used by the smoother:
+      // x + omega D^{-1}(b - A x) = x + omega (D^{-1} b - x - Ahat x)
+      BSR& S = H.Ahat_t[l];
+      S.nrows = S.ncols = n;
+      S.br = S.bc = np;
+      S.rowptr.assign(n + 1, 0);
+      for (i64 k = 0; k < n; ++k) S.rowptr[k + 1] = S.rowptr[k] + (T.rowptr[k + 1] - T.rowptr[k] - 1);
+      S.col.resize(S.rowptr[n]);
+      S.val.assign((size_t)S.rowptr[n] * nb2, 0.0);
+#pragma omp parallel for schedule(static)
+      for (i64 k = 0; k < n; ++k) {
+        i64 o = S.rowptr[k];
+        const double* Di = &H.Dinv_t[l][k * nb2];
+        for (i64 b = T.rowptr[k]; b < T.rowptr[k + 1]; ++b) {
+          if (T.col[b] == k) continue;
+          S.col[o] = T.col[b];
+          const double* Ab = T.block(b);
+          double* Sb = S.block(o);
+          for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+              double acc = 0.0;
+              for (int m = 0; m < np; ++m) acc += Di[i * np + m] * Ab[m * np + j];
+              Sb[i * np + j] = acc;
+            }
+          ++o;
+        }
+      }
+    }
     if (l + 1 < nlev) {
       H.L_t[l].resize((size_t)n * nb2);
       H.parent_t[l].resize(n);
@@ -478,8 +513,9 @@ void finalize_tree_order(Hierarchy& H) {
         for (int j = 0; j < np; ++j)
           dense[(size_t)(k * np + i) * nc + T.col[b] * np + j] = T.block(b)[i * np + j];
   H.coarse_inv.assign((size_t)nc * nc, 0.0);
-  if (!spd_inverse((int)nc, dense.data(), H.coarse_inv.data()))
-    throw std::runtime_error("coarsest operator not positive definite");
+  if (!spd_inverse((int)nc, dense.data(), H.coarse_inv.data()) &&
+      !lu_inverse((int)nc, dense.data(), H.coarse_inv.data()))
+    throw std::runtime_error("singular coarsest operator");
 }
 
 void build_rhs_data(Hierarchy& H) {

@@ -13,7 +13,7 @@ def declared():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
-            names += re.findall(r"^\s*(?:int|void|const char\*)\s+(cdg_\w+)\s*\(", txt, re.M)
+            names += re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(cdg_\w+)\s*\(", txt, re.M)
     return names
 
 

@@ -1,0 +1,64 @@
+"""Mixed precision (FP32 V-cycle inside the FP64 outer CG) against the FP64
+oracle.  The FP32 V-cycle is a different preconditioner from the FP64 one: its
+output differs by FP32 rounding (unit roundoff 6e-8, amplified by the smoother
+and transfers; bound used here 1e-4 relative).  The outer CG, its residual,
+dots and updates stay FP64, so the solution agrees with the FP64 oracle's to
+the solve tolerance: relative L2 difference <= 1e-9 and true residual
+<= 2e-10 ||b||.  The iteration count of the flexible (Polak-Ribiere) CG is
+reported next to the oracle's FP64 count."""
+import numpy as np
+import pytest
+
+from synthetic import jittered_square, kuhn_cube, sin_source
+from tests.gpu_common import OracleCase, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tri_p3_16": (lambda: jittered_square(16), dict(p=3, max_levels=4, nu_pre=2, nu_post=2)),
+    "tet_p2_4": (lambda: kuhn_cube(4), dict(p=2, max_levels=3)),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    from paper_2012_08024_gb300 import Solver
+    mk, kw = CASES[request.param]
+    mesh = mk()
+    S = Solver(mesh, precision="fp32", **kw).bind()
+    oc = OracleCase(mesh, kw["p"], kw["max_levels"], nu=kw.get("nu_pre", 1))
+    return S, oc
+
+
+def _t(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def test_fp32_vcycle_close_to_fp64_oracle(case):
+    import torch
+    S, oc = case
+    r = np.random.default_rng(5).standard_normal(oc.H.A[0].shape[0])
+    z = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    S.vcycle(_t(oc.to_tree(0, r)), z)
+    err = rel(oc.to_work(0, z.cpu().numpy()), oc.V.apply(r))
+    print(f"FP32 V-cycle relative error vs FP64 oracle: {err:.2e}")
+    assert err <= 1e-4
+
+
+def test_mixed_solve_matches_fp64_oracle(case):
+    from oracle.solver import pcg
+    S, oc = case
+    xq, _, _ = S.quadrature_points()
+    fq = sin_source(xq)
+    u, hist, it, rc = S.solve(_t(fq))
+    b = oc.L0.rhs(fq)
+    uo, ho, ito = pcg(oc.H.A[0], b, oc.V.apply, tol=1e-10)
+    err = rel(u.cpu().numpy(), uo)
+    res = np.linalg.norm(b - oc.H.A[0] @ u.cpu().numpy().ravel()) / np.linalg.norm(b)
+    print(f"mixed solve: iterations {it} (oracle FP64 {ito}), relative L2 vs oracle {err:.2e}, "
+          f"true residual {res:.2e}")
+    assert rc == 0 and hist[-1] <= 1e-10
+    assert res <= 2e-10
+    assert err <= 1e-9
+    assert it <= ito + 3
