@@ -907,7 +907,8 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
       if (res_hist) res_hist[it] = rr;
       if (!(hs[S_PQ] > 0.0) || !std::isfinite(rr)) {
         status = CDG_EBREAKDOWN;
-        h->err = "CG breakdown: p^T A p <= 0 or non-finite residual";
+        h->err = "CG breakdown at iteration " + std::to_string(it) + ": p^T A p = " + std::to_string(hs[S_PQ]) +
+                 ", (r, z) = " + std::to_string(hs[S_RZ]) + ", ||r||/||b|| = " + std::to_string(rr);
         break;
       }
       if (rr <= o.tol) break;
