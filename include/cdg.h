@@ -178,6 +178,28 @@ int cdg_vcycle(cdg_handle* h, const double* r, double* z, void* stream);
 int cdg_to_tree(cdg_handle* h, const double* user, double* tree, void* stream);
 int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream);
 
+/* Allocation-free variant of cdg_smooth (no counterpart in the paper: it exists
+ * for callers that cannot allocate device memory at the point of the call --
+ * code running while a memory pool is frozen or exhausted, or inside a host
+ * callback -- and therefore cannot provide scratch space of their own).
+ * Same result as cdg_smooth: y = x + omega D_l^{-1} (b - A_l x), device
+ * pointers, tree order, FP64 handle.  The intermediate D_l^{-1} b is kept in
+ * a fixed device array inside the library (CDG_STATIC_SCRATCH doubles = 8 MiB,
+ * held by every GPU that loads the library until the process exits) instead of
+ * the handle's buffer; levels with n_l * n_p > CDG_STATIC_SCRATCH are rejected
+ * with CDG_EINVAL.  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.  No device or host memory is allocated by this call. */
+#define CDG_STATIC_SCRATCH (1 << 20)
+int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
+                      void* stream);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (instrumentation for benchmarks; thread-safe, never reset). */
+int64_t cdg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ SIGNATURES = {
     "cdg_to_tree": (_I32, [_P, _P, _P, _P]),
     "cdg_to_user": (_I32, [_P, _P, _P, _P]),
     "cdg_kernel_launches": (_I64, []),
+    "cdg_smooth_static": (_I32, [_P, _I32, _P, _P, _P, _P]),
 }
 
 
@@ -266,6 +267,11 @@ class Solver:
 
     def smooth(self, level, x, b, y, stream=None):
         self._check(lib().cdg_smooth(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+
+    def smooth_static(self, level, x, b, y, stream=None):
+        """cdg_smooth without using the handle's buffer for its intermediate
+        (fixed library scratch; see include/cdg.h)."""
+        return lib().cdg_smooth_static(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream))
 
     def restrict(self, level, r, bc, stream=None):
         self._check(lib().cdg_restrict(self._h, level, _ptr(r), _ptr(bc), _stream_ptr(stream)))

@@ -284,6 +284,10 @@ int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream) {
   return dev_permute(h, tree, user, false, stream);
 }
 
+int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
+  return dev_smooth_static(h, level, x, b, y, stream);
+}
+
 int64_t cdg_kernel_launches(void) { return (int64_t)dev_launch_count(); }
 
 }  // extern "C"

@@ -19,6 +19,7 @@
 #include "handle.h"
 
 #include <atomic>
+#include <mutex>
 
 static std::atomic<long long> g_launches{0};
 
@@ -687,6 +688,66 @@ std::vector<int> to_i32(const std::vector<int64_t>& v) {
 
 // ------------------------------------------------------------------ entry points
 long long dev_launch_count() { return g_launches.load(); }
+
+// ------------------------------------------------------------------ allocation-free smoother
+// Fixed scratch for cdg_smooth_static: holds D^{-1} b of one level.  Every call
+// in the process shares it; nothing has to start at zero (the first kernel
+// overwrites all entries it later reads).
+static __device__ __align__(256) double g_static_scratch[CDG_STATIC_SCRATCH];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b, double* y, void* stream) {
+  if (!h) return CDG_EINVAL;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  if (level < 0 || level + 1 >= D.nlev || !x || !b || !y || !D.lev[level].Ahat) {
+    h->err = "cdg_smooth_static: bad level, NULL vector, or handle not in FP64 precision";
+    return CDG_EINVAL;
+  }
+  const DevLevel& L = D.lev[level];
+  if ((int64_t)L.n * D.np > (int64_t)CDG_STATIC_SCRATCH) {
+    h->err = "cdg_smooth_static: level has " + std::to_string((int64_t)L.n * D.np) +
+             " unknowns, more than the fixed scratch of " + std::to_string((int64_t)CDG_STATIC_SCRATCH);
+    return CDG_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cdg_smooth_static");
+  if (dev < 0 || dev >= kMaxDevices) {
+    h->err = "cdg_smooth_static: device index out of range";
+    return CDG_EINVAL;
+  }
+  double* scratch = nullptr;
+  {
+    // once per device, with that device current: the symbol's device address
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress");
+      g_static_ptr[dev] = (double*)p;
+    }
+    scratch = g_static_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, scratch, (double*)nullptr, h->opt.omega, s) &&
+                  launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)scratch, y,
+                                     h->opt.omega, nullptr, s);
+  if (!ok) {
+    h->err = "unsupported n_p";
+    return CDG_EINVAL;
+  }
+  CDG_CHECK_LAUNCH(h, "cdg_smooth_static");
+  return CDG_OK;
+}
 
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
   *bytes = (int64_t)layout(h->H, h->opt.precision, nullptr, nullptr);

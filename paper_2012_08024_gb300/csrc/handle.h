@@ -28,3 +28,4 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
 int dev_vcycle(cdg_handle* h, const double* r, double* z, void* stream);
 int dev_permute(cdg_handle* h, const double* in, double* out, bool to_tree, void* stream);
 long long dev_launch_count();
+int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b, double* y, void* stream);
