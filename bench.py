@@ -287,6 +287,26 @@ def main():
     achieved = alg_bytes / (k_us * 1e-6) / 1e9
     peak, peak_src = peaks()
     flops = 2.0 * nnzb0 * npb * npb
+    # ---- same workload with the FP32 V-cycle inside the FP64 CG (precision mode 1)
+    mixed = None
+    if prec == "fp64":
+        u64 = u.clone()
+        S32 = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision="fp32", tol=1e-10, maxit=500)
+        S32.bind(dev)
+        for _ in range(3):
+            u32, h32, it32, rc32 = S32.solve(fq)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            u32, h32, it32, rc32 = S32.solve(fq)
+        e1.record(stream)
+        barrier()
+        ms32 = e0.elapsed_time(e1) / args.steps
+        mixed = {"value": ndof * ws / (ms32 * 1e-3), "ms_per_step": ms32, "iterations": it32,
+                 "final_rel_residual": float(h32[-1]),
+                 "rel_l2_diff_vs_fp64_solve": float((u32 - u64).norm() / u64.norm()),
+                 "speedup_vs_fp64": ms / ms32}
+        del S32
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -311,6 +331,7 @@ def main():
                      "fp64_tflops": flops / (k_us * 1e-6) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS},
         "e2e": {"value": ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
+        "mixed_fp32_vcycle": mixed,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
