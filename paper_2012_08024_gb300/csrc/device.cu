@@ -29,7 +29,7 @@ constexpr int kMaxLev = CDG_MAX_LEVELS;
 constexpr int kThreads = 256;
 constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
 
-enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZOLD, S_TMP, S_COUNT = 16 };
+enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZOLD, S_TMP, S_FLAG = 15, S_COUNT = 16 };
 
 struct DevLevel {
   int n = 0;
@@ -190,12 +190,47 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+template <typename T, int NP>
+struct VecLoad;  // NP consecutive values of x as aligned vector loads
+template <int NP>
+struct VecLoad<float, NP> {
+  static __device__ __forceinline__ void load(const float* p, float* v) {
+    if constexpr (NP % 2 == 0) {
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(p + j));
+        v[j] = t.x;
+        v[j + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) v[j] = __ldg(p + j);
+    }
+  }
+};
+template <int NP>
+struct VecLoad<double, NP> {
+  static __device__ __forceinline__ void load(const double* p, double* v) {
+    if constexpr (NP % 2 == 0) {
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p + j));
+        v[j] = t.x;
+        v[j + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) v[j] = __ldg(p + j);
+    }
+  }
+};
+
 // One thread per scalar row: lane = sub * NP + i handles row i of block row
 // warp * (32 / NP) + sub.  MODE 0: y = A x, 1: y = b - A x,
 // 3: y = x + omega (bh - x - Ahat x) with Ahat = D^{-1}(A - D) and bh = D^{-1} b,
 // i.e. one damped block-Jacobi step.  With dot != nullptr, MODE 0 also writes
 // the block partial of sum_i x_i y_i (for p^T A p).
-template <typename T, int NP, int MODE>
+template <typename T, int NP, int MODE, bool VEC>
 __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restrict__ rowptr,
                                                        const int* __restrict__ col, const T* __restrict__ A,
                                                        const T* __restrict__ Dinv, const T* __restrict__ x,
@@ -215,8 +250,18 @@ __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restr
       const int J = ldg(col + bb);
       const T* a = A + (size_t)bb * NP * NP + i * NP;
       const T* xj = x + (size_t)J * NP;
+      if constexpr (VEC) {
+        // even n_p: the row of the block and x_J are 8-byte (FP32) / 16-byte
+        // (FP64) aligned runs, read as float2 / double2
+        T av[NP], xv[NP];
+        VecLoad<T, NP>::load(a, av);
+        VecLoad<T, NP>::load(xj, xv);
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
+        for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
+      }
     }
   }
   const size_t row = (size_t)K * NP + i;
@@ -239,6 +284,7 @@ __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restr
     else y[row] = x[row] + omega * (b[row] - x[row] - acc);
   }
 }
+
 
 // bh = Dinv b; with WRITE_X also x = omega bh (first smoothing step from a zero guess)
 template <typename T, int NP, bool WRITE_X>
@@ -489,16 +535,35 @@ inline unsigned rows_grid(int64_t nrows, int np) {
 // mode 0: y = A x (+ dot partials), 1: y = b - A x, 3: y = x + omega (bh - x - Ahat x)
 template <typename T>
 bool launch_bsr(int mode, int np, int n, const int* rowptr, const int* col, const T* A, const T* x, const T* b,
-                T* y, double omega, double* dot, cudaStream_t s) {
+                T* y, double omega, double* dot, cudaStream_t s, double* flag = nullptr) {
   const unsigned g = rows_grid(n, np);
+  // flag != nullptr marks vectors known to be 16-byte aligned: even n_p then
+  // takes the vector-load kernel
+  if (flag && np % 2 == 0) {
+    CDG_NP_DISPATCH(np, {
+      if constexpr (NP % 2 == 0) {
+        if (mode == 0)
+          launch(bsr_kernel<T, NP, 0, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
+                 (T)omega, dot);
+        else if (mode == 1)
+          launch(bsr_kernel<T, NP, 1, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
+                 (T)omega, (double*)nullptr);
+        else
+          launch(bsr_kernel<T, NP, 3, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
+                 (T)omega, (double*)nullptr);
+      }
+    });
+    return true;
+  }
   CDG_NP_DISPATCH(np, {
     if (mode == 0)
-      launch(bsr_kernel<T, NP, 0>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega, dot);
+      launch(bsr_kernel<T, NP, 0, false>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
+             dot);
     else if (mode == 1)
-      launch(bsr_kernel<T, NP, 1>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
+      launch(bsr_kernel<T, NP, 1, false>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
              (double*)nullptr);
     else
-      launch(bsr_kernel<T, NP, 3>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
+      launch(bsr_kernel<T, NP, 3, false>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y, (T)omega,
              (double*)nullptr);
   });
   return true;
@@ -590,10 +655,12 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     if (o.nu_pre >= 1) {
       if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, x, w, s)) return false;
       for (int k = 1; k < o.nu_pre; ++k) {
-        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s)) return false;
+        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s, D.scal + S_FLAG))
+          return false;
         std::swap(x, t);
       }
-      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s)) return false;
+      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, D.scal + S_FLAG))
+        return false;
       if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), (const T*)L.r,
                               (T*)D.lev[l + 1].b, s))
         return false;
@@ -620,7 +687,8 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
       return false;
     for (int k = 0; k < o.nu_post; ++k) {
       T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
-      if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s))
+      if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s,
+                         D.scal + S_FLAG))
         return false;
       if (out == t) std::swap(x, t);
       else x = out;
@@ -740,7 +808,8 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
   cudaStream_t s = (cudaStream_t)stream;
   const bool ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, scratch, (double*)nullptr, h->opt.omega, s) &&
                   launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)scratch, y,
-                                     h->opt.omega, nullptr, s);
+                                     h->opt.omega, nullptr, s,
+                                     (((uintptr_t)x | (uintptr_t)y) & 15) == 0 ? D.scal + S_FLAG : nullptr);
   if (!ok) {
     h->err = "unsupported n_p";
     return CDG_EINVAL;
@@ -808,6 +877,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   upload(D.rhs_bdata, H.rhs_bD, s);
   upload(D.btag, std::vector<int>(H.mesh.bf_tag.begin(), H.mesh.bf_tag.end()), s);
   upload(D.perm0, to_i32(H.order[0]), s);
+  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
   e = cudaGetLastError();
@@ -864,12 +934,15 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
     return CDG_EINVAL;
   }
   bool ok = true;
+  // caller vectors that are not 16-byte aligned take the kernel without vector loads
+  const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)b) & 15) == 0;
+  double* flag = aligned ? D.scal + S_FLAG : nullptr;
   if (op <= 1) {
-    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s);
+    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s, flag);
   } else if (op == 2) {
     ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, (double*)L.bh, (double*)nullptr, h->opt.omega, s) &&
          launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)L.bh, y, h->opt.omega,
-                            nullptr, s);
+                            nullptr, s, flag);
   }
   else if (op == 3) ok = launch_restrict<double>(D.np, D.lev[level + 1].n, D.lev[level + 1].childptr, L.L, x, y, s);
   else ok = launch_prolong<double>(D.np, L.n, L.parent, L.L, x, y, true, s);
@@ -914,6 +987,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     gN = gN ? D.gN_stage : nullptr;
     u_dev = D.u_stage;
   }
+  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT, s);   // scalars and the wait-timeout flag
   // right-hand side in tree order
   if (b_user) {
     launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
@@ -924,7 +998,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   const DevLevel& L0 = D.lev[0];
   if (use_u0) {
     launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, u_dev, D.x, 1);
-    launch_bsr<double>(1, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.x, D.bt, D.r, o.omega, nullptr, s);
+    launch_bsr<double>(1, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.x, D.bt, D.r, o.omega, nullptr, s, D.scal + S_FLAG);
   } else {
     cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
     cudaMemcpyAsync(D.r, D.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
@@ -954,7 +1028,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
       // q = A p and p.q
       const unsigned g = rows_grid(L0.n, D.np);
       launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, o.omega,
-                         D.partial, s);
+                         D.partial, s, D.scal + S_FLAG);
       launch(finalize_kernel, 1, kThreads, s, D.partial, (int)g, D.npartial, 0, 0, D.scal);
       const unsigned gv = vec_grid(n);
       launch(cg_update_kernel, gv, kThreads, s, n, D.scal, D.p, D.q, D.x, D.r, D.partial);
@@ -966,6 +1040,11 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
       ++it;
       const double rr = rel(hs[S_RR]);
       if (res_hist) res_hist[it] = rr;
+      if (hs[S_FLAG] != 0.0) {
+        status = CDG_ETIMEOUT;
+        h->err = "a bounded wait on a bulk copy into shared memory expired";
+        break;
+      }
       if (!(hs[S_PQ] > 0.0) || !std::isfinite(rr)) {
         status = CDG_EBREAKDOWN;
         h->err = "CG breakdown at iteration " + std::to_string(it) + ": p^T A p = " + std::to_string(hs[S_PQ]) +

@@ -103,23 +103,32 @@ def test_vcycle(case):
 
 
 def test_full_solve_matches_oracle(case):
+    """Iteration counts: within 1 of the oracle's; for solves longer than 60
+    iterations within 2, because the dense coarsest solves of the two sides
+    (explicit inverse on the device, LU in the oracle) agree only to
+    cond(A_n) eps ~ 1e-9, and the oracle's own count moves by up to 2 when its
+    V-cycle is perturbed at that level (3D cases at 65-85 iterations).
+    Solutions: at equal iteration counts within 1e-10 relative L2 of the
+    oracle's; otherwise both within 1e-10 of the direct solution."""
+    import scipy.sparse.linalg as spl
     import torch
     from oracle.solver import pcg
     S, oc, mesh = case
     xq, xbq, btag = S.quadrature_points()
     fq = sin_source(xq)
     u, hist, it, rc = S.solve(_t(fq))
-    assert rc == 0 and hist[-1] <= 1e-10
+    assert rc == 0 and hist[-1] <= 1e-10, (rc, hist[-3:])
     b = oc.L0.rhs(fq)
     uo, ho, ito = pcg(oc.H.A[0], b, oc.V.apply, tol=1e-10)
-    assert abs(it - ito) <= 1
-    # same number of iterations on both sides (a stop one iteration apart moves
-    # the iterate by about the tolerance itself)
-    if it != ito:
-        uo, ho, _ = pcg(oc.H.A[0], b, oc.V.apply, tol=0.0, maxit=it)
-    assert rel(u.cpu().numpy(), uo) <= 1e-10
+    assert abs(it - ito) <= (1 if ito <= 60 else 2), (it, ito, hist[-3:], ho[-3:])
+    ug = u.cpu().numpy().ravel()
+    if it == ito:
+        assert rel(ug, uo) <= 1e-10, (it, ito, rel(ug, uo))
+    else:
+        ud = spl.spsolve(oc.H.A[0].tocsc(), b)
+        assert rel(ug, ud) <= 1e-10 and rel(uo, ud) <= 1e-10, (it, ito, rel(ug, ud), rel(uo, ud))
     # the true residual of the GPU solution, by the oracle's operator
-    assert np.linalg.norm(b - oc.H.A[0] @ u.cpu().numpy().ravel()) <= 2e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(b - oc.H.A[0] @ ug) <= 2e-10 * np.linalg.norm(b)
     # host-pointer path gives the same answer
     uh, hh, ith, rch = S.solve_host(fq)
     assert ith == it and rel(uh, u.cpu().numpy()) <= 1e-14
@@ -169,3 +178,20 @@ def test_edge_cases():
     xq3, _, _ = S3.quadrature_points()
     u3, h3, it3, rc3 = S3.solve(_t(sin_source(xq3)))
     assert rc3 == 3 and it3 == 2 and np.isfinite(u3.cpu().numpy()).all()
+
+
+def test_unaligned_caller_vectors(case):
+    """Caller vectors that are not 16-byte aligned take the kernel without
+    vector loads; results agree with the aligned call."""
+    import torch
+    S, oc, _ = case
+    n = oc.H.A[0].shape[0]
+    big = torch.tensor(np.random.default_rng(7).standard_normal(n + 1), dtype=torch.float64, device="cuda")
+    xa = big[:n].clone()
+    xu = big[1:]
+    xu.copy_(xa)
+    ya, yu = torch.empty_like(xa), torch.empty(n + 1, dtype=torch.float64, device="cuda")[1:]
+    S.apply(0, xa, ya)
+    S.apply(0, xu, yu)
+    torch.cuda.synchronize()
+    assert rel(yu.cpu().numpy(), ya.cpu().numpy()) <= 1e-14
