@@ -5,10 +5,10 @@ fields, right-hand-side families).  It contains none of the method's
 arithmetic: no quadrature, basis, operator, agglomeration or solver code.
 """
 from .meshes import (jittered_square, kuhn_cube, batched_squares, square_with_holes,
-                     Mesh)
+                     Mesh, face_neighbors)
 from .fields import (sin_source, sin_solution, sine_combination_sources,
                      smoothed_lognormal_kappa)
 
-__all__ = ["jittered_square", "kuhn_cube", "batched_squares", "square_with_holes", "Mesh",
+__all__ = ["jittered_square", "kuhn_cube", "batched_squares", "square_with_holes", "Mesh", "face_neighbors",
            "sin_source", "sin_solution", "sine_combination_sources",
            "smoothed_lognormal_kappa"]

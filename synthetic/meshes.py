@@ -149,3 +149,19 @@ def square_with_holes(n: int, holes: tuple[tuple[int, int, int], ...] = ((2, 2, 
     d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
     xyz[~onb] += d[~onb]
     return Mesh(2, xyz, elem, bface, np.zeros(len(bface), dtype=np.int32))
+
+
+def face_neighbors(mesh: Mesh) -> list[np.ndarray]:
+    """Elements sharing a face with each element (combinatorics only)."""
+    d = mesh.dim
+    keys = {}
+    for K, e in enumerate(mesh.elem):
+        for i in range(d + 1):
+            keys.setdefault(tuple(sorted(int(v) for j, v in enumerate(e) if j != i)), []).append(K)
+    nb = [[] for _ in range(mesh.n_elements)]
+    for owners in keys.values():
+        if len(owners) == 2:
+            a, b = owners
+            nb[a].append(b)
+            nb[b].append(a)
+    return [np.array(sorted(x), dtype=np.int64) for x in nb]
