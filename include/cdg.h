@@ -156,6 +156,24 @@ int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double
 int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist,
                 int32_t* iters, void* stream);
 
+/* Adjoint (differentiation of the solve; the paper has no adjoint, it follows
+ * from the primal form eq. primal_form, A_0(kappa) u = b(f, kappa)).  For a loss
+ * L(u): lambda solves A_0^T lambda = dL/du; dL/df = (db/df)^T lambda and
+ * dL/dkappa_K = lambda^T (db/dkappa_K - dA_0/dkappa_K u).  A_0 is symmetric, so
+ * the adjoint solve is the same preconditioned CG.  All vectors device, user
+ * order; these calls use the handle's CG work vectors (do not overlap them with
+ * a solve on another stream). */
+/* lambda [n_elements][n_p] from dLdu [n_elements][n_p]; as cdg_solve_b. */
+int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,
+                      void* stream);
+/* dLdf_q [n_elements][nq]: sum_i w_q phi_i(x_q) lambda_K[i]. */
+int cdg_rhs_adjoint(cdg_handle* h, const double* lambda, double* dLdf_q, void* stream);
+/* dLdkappa [n_elements]: each term of A_0 and b is owned by one element and is
+ * linear in its kappa (R7: volume term by its element, interior face by its
+ * q-side, Dirichlet face by its element); gD_q as in cdg_rhs (NULL = 0). */
+int cdg_kappa_gradient(cdg_handle* h, const double* lambda, const double* u, const double* gD_q, double* dLdkappa,
+                       void* stream);
+
 /* Per-level operations (device pointers, tree order, FP64): */
 /* y = A_l x  (block-sparse apply, eq. primal_form and Section 4.1) */
 int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream);

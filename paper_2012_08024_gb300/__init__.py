@@ -78,6 +78,9 @@ SIGNATURES = {
     "cdg_to_user": (_I32, [_P, _P, _P, _P]),
     "cdg_kernel_launches": (_I64, []),
     "cdg_smooth_static": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "cdg_solve_adjoint": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "cdg_rhs_adjoint": (_I32, [_P, _P, _P, _P]),
+    "cdg_kappa_gradient": (_I32, [_P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -252,6 +255,29 @@ class Solver:
         if rc not in (0, 3):
             self._check(rc)
         return u, hist[:it.value + 1], it.value, rc
+
+    def solve_adjoint(self, dLdu, stream=None):
+        import torch
+        lam = torch.empty((self.ne, self.np_), dtype=torch.float64, device=dLdu.device)
+        hist = np.zeros(self.maxit + 1)
+        it = C.c_int32(0)
+        rc = lib().cdg_solve_adjoint(self._h, _ptr(dLdu), _ptr(lam), hist.ctypes.data, C.byref(it),
+                                     _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return lam, hist[:it.value + 1], it.value, rc
+
+    def rhs_adjoint(self, lam, stream=None):
+        import torch
+        out = torch.empty((self.ne, self.info["nq"]), dtype=torch.float64, device=lam.device)
+        self._check(lib().cdg_rhs_adjoint(self._h, _ptr(lam), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def kappa_gradient(self, lam, u, gD=None, stream=None):
+        import torch
+        out = torch.empty(self.ne, dtype=torch.float64, device=lam.device)
+        self._check(lib().cdg_kappa_gradient(self._h, _ptr(lam), _ptr(u), _ptr(gD), _ptr(out), _stream_ptr(stream)))
+        return out
 
     def rhs(self, f_q, gD=None, gN=None, stream=None):
         import torch

@@ -288,6 +288,23 @@ int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const doubl
   return dev_smooth_static(h, level, x, b, y, stream);
 }
 
+int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,
+                      void* stream) {
+  // A_0 is symmetric: A^T lambda = dL/du is the same solve as A_0 u = b
+  return cdg_solve_b(h, dLdu, lambda, 0, res_hist, iters, stream);
+}
+
+int cdg_rhs_adjoint(cdg_handle* h, const double* lambda, double* dLdf_q, void* stream) {
+  if (!h || !lambda || !dLdf_q) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  return dev_adjoint(h, 0, lambda, nullptr, nullptr, dLdf_q, stream);
+}
+
+int cdg_kappa_gradient(cdg_handle* h, const double* lambda, const double* u, const double* gD_q, double* dLdkappa,
+                       void* stream) {
+  if (!h || !lambda || !u || !dLdkappa) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  return dev_adjoint(h, 1, lambda, u, gD_q, dLdkappa, stream);
+}
+
 int64_t cdg_kernel_launches(void) { return (int64_t)dev_launch_count(); }
 
 }  // extern "C"

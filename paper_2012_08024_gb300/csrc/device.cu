@@ -75,6 +75,12 @@ struct DeviceState {
   double* rhs_bdata = nullptr;
   int* btag = nullptr;
   int* perm0 = nullptr;         // tree row -> user element
+  // d A_0 / d kappa pieces (tree order)
+  double* dk_own = nullptr;
+  int* dk_ptr = nullptr;
+  int* dk_nbr = nullptr;
+  double* dk_blk = nullptr;
+  double* kappa = nullptr;
   // CG vectors (FP64, tree order)
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr,
          *zold = nullptr;
@@ -165,6 +171,11 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
   D.rhs_bdata = c.take<double>(H.rhs_bD.size() + 1);
   D.btag = c.take<int>(D.nbf + 1);
   D.perm0 = c.take<int>(ne);
+  D.dk_own = c.take<double>(H.dk_own.size() + 1);
+  D.dk_ptr = c.take<int>(H.dk_ptr.size());
+  D.dk_nbr = c.take<int>(H.dk_nbr.size() + 1);
+  D.dk_blk = c.take<double>(H.dk_blk.size() + 1);
+  D.kappa = c.take<double>(H.kappa_w.size());
   D.x = c.take<double>(vecbytes_elems);
   D.r = c.take<double>(vecbytes_elems);
   D.z = c.take<double>(vecbytes_elems);
@@ -502,6 +513,81 @@ __global__ void permute_kernel(int ne, int np, const int* __restrict__ perm0, co
     if (to_tree) out[k * np + i] = in[K * np + i];
     else out[K * np + i] = in[k * np + i];
   }
+}
+
+
+// dL/dkappa_K = lambda^T (db/dkappa_K - dA/dkappa_K u): A_0 and b are linear in
+// kappa (every term is owned by one element, R7), so dA/dkappa_K is the
+// unit-kappa sum of K's own pieces.  Thread (sub, i) of the usual row mapping
+// accumulates row i of every piece; the NP lanes of an element then reduce.
+template <int NP>
+__global__ void __launch_bounds__(kThreads) kappa_grad_kernel(
+    int ne, int nfq, const int* __restrict__ perm0, const double* __restrict__ own, const int* __restrict__ ptr,
+    const int* __restrict__ nbr, const double* __restrict__ blk, const double* __restrict__ kappa,
+    const double* __restrict__ lam, const double* __restrict__ u, const int* __restrict__ bptr,
+    const int* __restrict__ bface, const double* __restrict__ bdata, const int* __restrict__ btag,
+    const double* __restrict__ gD, double* __restrict__ out) {
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int k = warp * RPW + sub;
+  const bool active = (sub < RPW) && (k < ne);
+  double t = 0.0;
+  if (active) {
+    const double* uk = u + (size_t)k * NP;
+    const double lk = lam[(size_t)k * NP + i];
+    const double* O = own + (size_t)k * NP * NP + i * NP;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s = fma(O[j], uk[j], s);
+    t = -lk * s;
+    for (int f = ptr[k]; f < ptr[k + 1]; ++f) {
+      const int J = nbr[f];
+      const double* uJ = u + (size_t)J * NP;
+      const double lJ = lam[(size_t)J * NP + i];
+      const double* B = blk + (size_t)f * 3 * NP * NP + i * NP;
+      double s_kj = 0.0, s_jk = 0.0, s_jj = 0.0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        s_kj = fma(B[j], uJ[j], s_kj);
+        s_jk = fma(B[NP * NP + j], uk[j], s_jk);
+        s_jj = fma(B[2 * NP * NP + j], uJ[j], s_jj);
+      }
+      t -= lk * s_kj + lJ * (s_jk + s_jj);
+    }
+    if (gD) {
+      const double ik = 1.0 / kappa[k];
+      for (int b = bptr[k]; b < bptr[k + 1]; ++b) {
+        const int bf = bface[b];
+        if (btag[bf] != 0) continue;
+        const double* Bd = bdata + (size_t)bf * nfq * NP + i;
+        double s2 = 0.0;
+        for (int q = 0; q < nfq; ++q) s2 = fma(Bd[(size_t)q * NP], gD[(size_t)bf * nfq + q], s2);
+        t += lk * s2 * ik;
+      }
+    }
+  }
+  double g = 0.0;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) g += __shfl_sync(0xffffffffu, t, sub * NP + j);
+  if (active && i == 0) out[perm0[k]] = g;
+}
+
+// dL/df_q = (db/df)^T lambda: out[K][q] = sum_i w_q phi_i(x_q) lambda_K[i] (user order)
+template <int NP>
+__global__ void rhs_adjoint_kernel(int ne, int nq, const int* __restrict__ perm0, const double* __restrict__ V,
+                                   const double* __restrict__ lam, double* __restrict__ out) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)ne * nq) return;
+  const size_t k = t / nq, q = t - k * nq;
+  const double* Vq = V + (k * nq + q) * NP;
+  const double* lk = lam + k * NP;
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) s = fma(Vq[i], lk[i], s);
+  out[(size_t)perm0[k] * nq + q] = s;
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -877,6 +963,11 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   upload(D.rhs_bdata, H.rhs_bD, s);
   upload(D.btag, std::vector<int>(H.mesh.bf_tag.begin(), H.mesh.bf_tag.end()), s);
   upload(D.perm0, to_i32(H.order[0]), s);
+  upload(D.dk_own, H.dk_own, s);
+  upload(D.dk_ptr, to_i32(H.dk_ptr), s);
+  upload(D.dk_nbr, to_i32(H.dk_nbr), s);
+  upload(D.dk_blk, H.dk_blk, s);
+  upload(D.kappa, H.kappa_w, s);
   cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
@@ -1066,4 +1157,30 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   *iters = it;
   if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
   return status;
+}
+
+int dev_adjoint(cdg_handle* h, int what, const double* lam_user, const double* u_user, const double* gD,
+                double* out, void* stream) {
+  if (!h) return CDG_EINVAL;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)D.ndofs;
+  // lambda (and u) to tree order in the CG work vectors (free outside a solve)
+  launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, lam_user, D.r, 1);
+  if (what == 0) {
+    const size_t tot = (size_t)D.ne * D.nq;
+    CDG_NP_DISPATCH(D.np, launch(rhs_adjoint_kernel<NP>, (unsigned)((tot + 255) / 256), 256, s, (int)D.ne, D.nq,
+                                 D.perm0, D.rhs_vol, D.r, out));
+  } else {
+    launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, u_user, D.z, 1);
+    CDG_NP_DISPATCH(D.np, launch(kappa_grad_kernel<NP>, rows_grid(D.ne, D.np), kThreads, s, (int)D.ne, D.nfq,
+                                 D.perm0, D.dk_own, D.dk_ptr, D.dk_nbr, D.dk_blk, D.kappa, D.r, D.z, D.rhs_bptr,
+                                 D.rhs_bface, D.rhs_bdata, D.btag, gD, out));
+  }
+  CDG_CHECK_LAUNCH(h, "adjoint");
+  return CDG_OK;
 }

@@ -29,3 +29,5 @@ int dev_vcycle(cdg_handle* h, const double* r, double* z, void* stream);
 int dev_permute(cdg_handle* h, const double* in, double* out, bool to_tree, void* stream);
 long long dev_launch_count();
 int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b, double* y, void* stream);
+int dev_adjoint(cdg_handle* h, int what, const double* lam_user, const double* u_user, const double* gD,
+                double* out, void* stream);

@@ -125,6 +125,15 @@ struct Hierarchy {
   std::vector<i64> rhs_bptr;                  // [ne+1] boundary faces of each element
   std::vector<i64> rhs_bface;                 // boundary face ids
   std::vector<double> rhs_bD, rhs_bN;         // [nbf][nfq][np]
+  // d A_0 / d kappa_K (R7: A_0 is linear in kappa), per element, unit-kappa pieces:
+  // own block (volume + Dirichlet faces + q-side diagonal parts) and, for each
+  // face where K is the q-side, the (K,J), (J,K), (J,J) blocks.  Working order
+  // after build_level0, tree order (rows and J) after build_rhs_data.
+  std::vector<double> dk_own;                 // [ne][np][np]
+  std::vector<i64> dk_ptr;                    // [ne+1] q-faces of each element
+  std::vector<i64> dk_nbr;                    // neighbour J of each q-face
+  std::vector<double> dk_blk;                 // [nq_faces][3][np][np]: KJ, JK, JJ
+  std::vector<double> kappa_w;                // kappa per element (working order), 1 if none
   // timings
   double t_mesh = 0, t_assemble = 0, t_agglomerate = 0, t_coarsen = 0;
 };

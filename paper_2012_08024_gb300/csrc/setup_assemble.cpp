@@ -223,6 +223,41 @@ void build_level0(Hierarchy& H) {
       for (int i = 0; i < np; ++i) H.rhs_vol[((size_t)K * nq + q) * np + i] = w * ph[i];
     }
 
+  // unit-kappa pieces of A_0 owned by each element (for d A_0 / d kappa)
+  H.kappa_w.assign(ne, 1.0);
+  for (i64 K = 0; K < ne; ++K) H.kappa_w[K] = kap(H.opt, K);
+  H.dk_own.assign((size_t)ne * nb2, 0.0);
+  H.dk_ptr.assign(ne + 1, 0);
+  for (i64 f = 0; f < nif; ++f) ++H.dk_ptr[m.if_q[f] + 1];
+  for (i64 K = 0; K < ne; ++K) H.dk_ptr[K + 1] += H.dk_ptr[K];
+  H.dk_nbr.assign(nif, 0);
+  H.dk_blk.assign((size_t)nif * 3 * nb2, 0.0);
+  {
+    std::vector<i64> fill(H.dk_ptr.begin(), H.dk_ptr.end() - 1);
+    for (i64 f = 0; f < nif; ++f) {   // ascending face order inside each element
+      const i64 K = m.if_q[f];
+      const i64 t = fill[K]++;
+      H.dk_nbr[t] = m.if_u[f];
+      const double ik = 1.0 / kap(H.opt, K);
+      for (size_t e = 0; e < nb2; ++e) {
+        H.dk_own[K * nb2 + e] += ik * Fb[(f * 4 + 0) * nb2 + e];
+        H.dk_blk[(t * 3 + 0) * nb2 + e] = ik * Fb[(f * 4 + 1) * nb2 + e];
+        H.dk_blk[(t * 3 + 1) * nb2 + e] = ik * Fb[(f * 4 + 2) * nb2 + e];
+        H.dk_blk[(t * 3 + 2) * nb2 + e] = ik * Fb[(f * 4 + 3) * nb2 + e];
+      }
+    }
+  }
+  for (i64 K = 0; K < ne; ++K) {
+    const double ik = 1.0 / kap(H.opt, K);
+    for (size_t e = 0; e < nb2; ++e) H.dk_own[K * nb2 + e] += ik * Vb[K * nb2 + e];
+  }
+  for (i64 bfi = 0; bfi < nbf; ++bfi)
+    if (m.bf_tag[bfi] == 0) {
+      const i64 K = m.bf_K[bfi];
+      const double ik = 1.0 / kap(H.opt, K);
+      for (size_t e = 0; e < nb2; ++e) H.dk_own[K * nb2 + e] += ik * Db[bfi * nb2 + e];
+    }
+
   // assemble A_0 rows: diagonal + face neighbours, sorted columns
   BSR& A = L0.A;
   A.nrows = A.ncols = ne;

@@ -522,6 +522,29 @@ void build_rhs_data(Hierarchy& H) {
   const Mesh0& m = H.mesh;
   const int np = H.np, nq = H.vrule.n();
   const i64 ne = m.ne;
+  const size_t nb2 = (size_t)np * np;
+  // d A / d kappa pieces to tree order (rows and neighbour indices)
+  {
+    const std::vector<i64>& ord = H.order[0];
+    const std::vector<i64>& pos = H.pos[0];
+    std::vector<double> own((size_t)ne * nb2), blk(H.dk_blk.size()), kap(ne);
+    std::vector<i64> ptr(ne + 1, 0), nbr(H.dk_nbr.size());
+    for (i64 k = 0; k < ne; ++k) ptr[k + 1] = ptr[k] + (H.dk_ptr[ord[k] + 1] - H.dk_ptr[ord[k]]);
+    for (i64 k = 0; k < ne; ++k) {
+      const i64 K = ord[k];
+      kap[k] = H.kappa_w[K];
+      std::memcpy(&own[k * nb2], &H.dk_own[K * nb2], nb2 * sizeof(double));
+      for (i64 t = H.dk_ptr[K], o = ptr[k]; t < H.dk_ptr[K + 1]; ++t, ++o) {
+        nbr[o] = pos[H.dk_nbr[t]];
+        std::memcpy(&blk[o * 3 * nb2], &H.dk_blk[t * 3 * nb2], 3 * nb2 * sizeof(double));
+      }
+    }
+    H.dk_own.swap(own);
+    H.dk_blk.swap(blk);
+    H.dk_ptr.swap(ptr);
+    H.dk_nbr.swap(nbr);
+    H.kappa_w.swap(kap);
+  }
   // volume data to tree order
   std::vector<double> v((size_t)ne * nq * np);
   for (i64 k = 0; k < ne; ++k)
