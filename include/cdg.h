@@ -96,6 +96,7 @@ typedef struct {
   double h_avg, C_D;
   int64_t device_bytes;     /* size of the buffer cdg_bind_device needs */
   double setup_seconds[4];  /* mesh, level-0 assembly, agglomeration, coarsening */
+  int32_t n_meshes;         /* 1, or the number of meshes of a batched handle */
 } cdg_info;
 
 /* Defaults: p=2, gamma=1e4, V(1,1), omega=2/3, 4 levels, seed 0, FP64,
@@ -108,6 +109,20 @@ void cdg_default_options(cdg_options* opt);
  * Errors: CDG_EINVAL, CDG_EMESH, CDG_ENOMEM. */
 int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out);
 void cdg_destroy(cdg_handle* h);
+
+/* Batched handle: n_meshes independent meshes (same dim, p and options, and
+ * the same number of hierarchy levels) set up separately and solved together.
+ * Every level is the block-diagonal union of the meshes' levels, so each kernel
+ * of the solve phase processes all meshes in one launch; the CG keeps separate
+ * scalars and convergence per mesh (a converged mesh stops changing).  Arrays
+ * of a batched handle concatenate the meshes in order (elements, boundary
+ * faces, dofs; offsets from cdg_batch_offsets); cdg_solve then writes
+ * res_hist[n_meshes][maxit+1] and iters[n_meshes].  kappa, face_switch and
+ * enumeration must be NULL.  The paper solves one mesh at a time; batching is
+ * an execution choice of this library. */
+int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_options* opt, cdg_handle** out);
+/* n_meshes, elem_offsets [n_meshes+1] and bface_offsets [n_meshes+1] (any may be NULL). */
+int cdg_batch_offsets(const cdg_handle* h, int32_t* n_meshes, int64_t* elem_offsets, int64_t* bface_offsets);
 const char* cdg_last_error(const cdg_handle* h);
 int cdg_query(const cdg_handle* h, cdg_info* info);
 
@@ -147,7 +162,8 @@ int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD_q, const double* 
  * maxit+1 entries) and *iters.  host_pointers != 0: f_q, gD_q, gN_q, u and
  * res_hist are host arrays (copied in and out inside the call); else device
  * arrays (res_hist may then be a host array too: it is always written from
- * the host).  Synchronises stream.  Errors: CDG_ESTATE, CDG_ENOCONV,
+ * the host).  The solve runs on a private stream of the handle, ordered after
+ * the work already queued on `stream`; it returns when the solution is written.  Errors: CDG_ESTATE, CDG_ENOCONV,
  * CDG_EBREAKDOWN, CDG_ECUDA. */
 int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double* gN_q, double* u,
               int32_t use_u0, double* res_hist, int32_t* iters, int32_t host_pointers, void* stream);

@@ -47,7 +47,7 @@ class cdg_info(C.Structure):
                 ("n_interior_faces", C.c_int64), ("n_bfaces", C.c_int64), ("n_dofs", C.c_int64),
                 ("n_l", C.c_int64 * CDG_MAX_LEVELS), ("nnzb_l", C.c_int64 * CDG_MAX_LEVELS),
                 ("h_avg", C.c_double), ("C_D", C.c_double), ("device_bytes", C.c_int64),
-                ("setup_seconds", C.c_double * 4)]
+                ("setup_seconds", C.c_double * 4), ("n_meshes", C.c_int32)]
 
 
 _lib = None
@@ -57,6 +57,8 @@ _P, _I32, _I64, _D, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uin
 SIGNATURES = {
     "cdg_default_options": (None, [_P]),
     "cdg_create": (_I32, [_P, _P, _P]),
+    "cdg_create_batched": (_I32, [_P, _I32, _P, _P]),
+    "cdg_batch_offsets": (_I32, [_P, _P, _P, _P]),
     "cdg_destroy": (None, [_P]),
     "cdg_last_error": (C.c_char_p, [_P]),
     "cdg_query": (_I32, [_P, _P]),
@@ -316,3 +318,66 @@ class Solver:
 
     def to_user(self, tree, user, stream=None):
         self._check(lib().cdg_to_user(self._h, _ptr(tree), _ptr(user), _stream_ptr(stream)))
+
+
+class BatchSolver(Solver):
+    """Many independent meshes in one handle (cdg_create_batched): every kernel
+    of the solve phase processes all meshes per launch; per-mesh CG scalars."""
+
+    def __init__(self, meshes, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
+                 omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
+                 switch_kind: int = 0, coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500):
+        L = lib()
+        keep, ms = [], (cdg_mesh * len(meshes))()
+        for i, mesh in enumerate(meshes):
+            xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+            elem = np.ascontiguousarray(mesh.elem, dtype=np.int64)
+            bface = np.ascontiguousarray(mesh.bface, dtype=np.int64).reshape(-1, mesh.dim)
+            btag = np.ascontiguousarray(mesh.btag, dtype=np.int32)
+            keep += [xyz, elem, bface, btag]
+            ms[i] = cdg_mesh(mesh.dim, xyz.shape[0], xyz.ctypes.data, elem.shape[0], elem.ctypes.data,
+                             bface.shape[0], bface.ctypes.data if len(bface) else None,
+                             btag.ctypes.data if len(btag) else None)
+        o = cdg_options()
+        L.cdg_default_options(C.byref(o))
+        o.p, o.gamma, o.nu_pre, o.nu_post, o.omega = p, gamma, nu_pre, nu_post, omega
+        o.max_levels, o.seed = max_levels, seed
+        o.precision, o.switch_kind = PRECISION[precision], switch_kind
+        o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
+        h = C.c_void_p()
+        rc = L.cdg_create_batched(ms, len(meshes), C.byref(o), C.byref(h))
+        if rc:
+            raise CdgError(rc, L.cdg_last_error(None).decode())
+        self._h = h
+        self.precision = precision
+        self.buffer = None
+        inf = cdg_info()
+        L.cdg_query(h, C.byref(inf))
+        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l") else
+                         list(getattr(inf, k)) if k == "setup_seconds" else getattr(inf, k))
+                     for k, _ in cdg_info._fields_}
+        self.np_ = inf.n_p
+        self.n_levels = inf.n_levels
+        self.ne = inf.n_elements
+        self.maxit = maxit
+        self.n_meshes = inf.n_meshes
+        self.elem_offsets = np.zeros(self.n_meshes + 1, dtype=np.int64)
+        self.bface_offsets = np.zeros(self.n_meshes + 1, dtype=np.int64)
+        L.cdg_batch_offsets(h, None, self.elem_offsets.ctypes.data, self.bface_offsets.ctypes.data)
+
+    def solve(self, f_q, gD=None, gN=None, u0=None, stream=None):
+        """Device tensors (all meshes concatenated); returns u, per-mesh residual
+        histories (list), per-mesh iteration counts (array), status."""
+        import torch
+        u = torch.empty((self.ne, self.np_), dtype=torch.float64, device=f_q.device) if u0 is None else u0
+        hist = np.zeros((self.n_meshes, self.maxit + 1))
+        its = np.zeros(self.n_meshes, dtype=np.int32)
+        rc = lib().cdg_solve(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(u), 0 if u0 is None else 1,
+                             hist.ctypes.data, its.ctypes.data, 0, _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return u, [hist[m, :its[m] + 1] for m in range(self.n_meshes)], its, rc
+
+    solve_host = None
+    solve_b = None
+    solve_adjoint = None

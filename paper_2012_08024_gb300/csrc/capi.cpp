@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <stdexcept>
+#include <vector>
 
 #include "handle.h"
 
@@ -21,6 +22,126 @@ int fail(cdg_handle* h, int code, const std::string& msg) {
   return code;
 }
 }  // namespace
+
+static int check_options(const cdg_options* opt) {
+  if (opt->p < 1 || opt->p > 6) return fail(nullptr, CDG_EINVAL, "p must be in [1, 6]");
+  if (opt->max_levels < 1 || opt->max_levels > CDG_MAX_LEVELS)
+    return fail(nullptr, CDG_EINVAL, "max_levels must be in [1, 16]");
+  if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->nu_pre + opt->nu_post < 1)
+    return fail(nullptr, CDG_EINVAL, "need nu_pre, nu_post >= 0 and at least one smoothing step");
+  if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0))
+    return fail(nullptr, CDG_EINVAL, "bad omega, gamma, tol or maxit");
+  if (opt->precision < 0 || opt->precision > 1) return fail(nullptr, CDG_EINVAL, "precision must be 0 or 1");
+  return CDG_OK;
+}
+
+static int check_mesh(const cdg_mesh* mesh) {
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, CDG_EINVAL, "dim must be 2 or 3");
+  if (mesh->n_elements <= 0 || mesh->n_vertices <= 0 || !mesh->xyz || !mesh->elem)
+    return fail(nullptr, CDG_EINVAL, "empty mesh");
+  if (mesh->n_bfaces < 0 || (mesh->n_bfaces > 0 && !mesh->bface))
+    return fail(nullptr, CDG_EINVAL, "bad boundary face list");
+  return CDG_OK;
+}
+
+// Host set-up of one mesh (throws on bad input).  kappa / enumeration / switch
+// are taken from opt only when use_arrays is set (single-mesh handles).
+static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arrays, cdg::Hierarchy& H) {
+  cdg::Options& o = H.opt;
+  o.p = opt->p;
+  o.gamma = opt->gamma;
+  o.nu_pre = opt->nu_pre;
+  o.nu_post = opt->nu_post;
+  o.omega = opt->omega;
+  o.max_levels = opt->max_levels;
+  o.seed = opt->seed;
+  o.switch_kind = opt->switch_kind;
+  o.coarsen = opt->coarsen;
+  const int64_t ne = mesh->n_elements;
+  if (use_arrays && opt->enumeration) o.enumeration.assign(opt->enumeration, opt->enumeration + ne);
+  if (use_arrays && opt->kappa) {
+    o.kappa.assign(opt->kappa, opt->kappa + ne);
+    for (double k : o.kappa)
+      if (!(k > 0) || !std::isfinite(k)) throw std::invalid_argument("kappa must be positive and finite");
+  }
+  double t0 = now();
+  cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces, mesh->bface,
+                  mesh->btag, o, H.mesh);
+  if (use_arrays && opt->face_switch) {
+    const size_t nif = H.mesh.if_K1.size();
+    o.face_switch.assign(opt->face_switch, opt->face_switch + nif);
+    cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces, mesh->bface,
+                    mesh->btag, o, H.mesh);
+  }
+  H.mono.init(mesh->dim, o.p);
+  H.np = H.mono.np;
+  H.vrule = cdg::simplex_rule(mesh->dim, 2 * o.p);
+  H.frule = cdg::simplex_rule(mesh->dim - 1, 2 * o.p);
+  H.lev.assign(1, cdg::Level());
+  double t1 = now();
+  cdg::build_level0(H);
+  double t2 = now();
+  cdg::agglomerate(H);
+  double t3 = now();
+  cdg::coarsen(H);
+  cdg::finalize_tree_order(H);
+  cdg::build_rhs_data(H);
+  double t4 = now();
+  H.t_mesh = t1 - t0;
+  H.t_assemble = t2 - t1;
+  H.t_agglomerate = t3 - t2;
+  H.t_coarsen = t4 - t3;
+}
+
+template <typename F>
+static int guarded(cdg_handle* h, F&& f) {
+  try {
+    f();
+  } catch (const std::invalid_argument& e) {
+    delete h;
+    return fail(nullptr, CDG_EINVAL, e.what());
+  } catch (const std::domain_error& e) {
+    delete h;
+    return fail(nullptr, CDG_EMESH, e.what());
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(nullptr, CDG_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    delete h;
+    return fail(nullptr, CDG_EMESH, e.what());
+  }
+  return CDG_OK;
+}
+
+static void quad_points(const cdg::Hierarchy& H, double* xq, double* xbq, int32_t* btag) {
+  const cdg::Mesh0& m = H.mesh;
+  const int d = m.d;
+  if (xq) {
+    const int nq = H.vrule.n();
+    for (int64_t K = 0; K < m.ne; ++K) {
+      const int64_t* ev = m.elem.data() + K * (d + 1);
+      for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < d; ++k) {
+          double s = m.xyz[ev[0] * d + k];
+          for (int i = 0; i < d; ++i)
+            s += H.vrule.x[(size_t)q * d + i] * (m.xyz[ev[i + 1] * d + k] - m.xyz[ev[0] * d + k]);
+          xq[((size_t)K * nq + q) * d + k] = s;
+        }
+    }
+  }
+  const int nfq = H.frule.n();
+  for (size_t b = 0; b < m.bf_K.size(); ++b) {
+    if (btag) btag[b] = m.bf_tag[b];
+    if (!xbq) continue;
+    const double* xv = &m.bf_xv[b * d * d];
+    for (int q = 0; q < nfq; ++q)
+      for (int k = 0; k < d; ++k) {
+        double s = xv[k];
+        for (int i = 0; i < d - 1; ++i) s += H.frule.x[(size_t)q * (d - 1) + i] * (xv[(i + 1) * d + k] - xv[k]);
+        xbq[((size_t)b * nfq + q) * d + k] = s;
+      }
+  }
+}
 
 extern "C" {
 
@@ -49,88 +170,66 @@ int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out) {
   if (!out) return fail(nullptr, CDG_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !opt) return fail(nullptr, CDG_EINVAL, "mesh or options NULL");
-  if (opt->p < 1 || opt->p > 6) return fail(nullptr, CDG_EINVAL, "p must be in [1, 6]");
-  if (opt->max_levels < 1 || opt->max_levels > CDG_MAX_LEVELS)
-    return fail(nullptr, CDG_EINVAL, "max_levels must be in [1, 16]");
-  if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->nu_pre + opt->nu_post < 1)
-    return fail(nullptr, CDG_EINVAL, "need nu_pre, nu_post >= 0 and at least one smoothing step");
-  if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0))
-    return fail(nullptr, CDG_EINVAL, "bad omega, gamma, tol or maxit");
-  if (opt->precision < 0 || opt->precision > 1) return fail(nullptr, CDG_EINVAL, "precision must be 0 or 1");
-  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, CDG_EINVAL, "dim must be 2 or 3");
-  if (mesh->n_elements <= 0 || mesh->n_vertices <= 0 || !mesh->xyz || !mesh->elem)
-    return fail(nullptr, CDG_EINVAL, "empty mesh");
-  if (mesh->n_bfaces < 0 || (mesh->n_bfaces > 0 && !mesh->bface))
-    return fail(nullptr, CDG_EINVAL, "bad boundary face list");
-  cdg_handle* h = nullptr;
-  try {
-    h = new cdg_handle();
-    h->opt = *opt;
-    h->opt.face_switch = nullptr;
-    h->opt.enumeration = nullptr;
-    h->opt.kappa = nullptr;
-    cdg::Hierarchy& H = h->H;
-    cdg::Options& o = H.opt;
-    o.p = opt->p;
-    o.gamma = opt->gamma;
-    o.nu_pre = opt->nu_pre;
-    o.nu_post = opt->nu_post;
-    o.omega = opt->omega;
-    o.max_levels = opt->max_levels;
-    o.seed = opt->seed;
-    o.switch_kind = opt->switch_kind;
-    o.coarsen = opt->coarsen;
-    const int64_t ne = mesh->n_elements;
-    if (opt->enumeration) o.enumeration.assign(opt->enumeration, opt->enumeration + ne);
-    if (opt->kappa) {
-      o.kappa.assign(opt->kappa, opt->kappa + ne);
-      for (double k : o.kappa)
-        if (!(k > 0) || !std::isfinite(k)) {
-          delete h;
-          return fail(nullptr, CDG_EINVAL, "kappa must be positive and finite");
-        }
-    }
-    double t0 = now();
-    cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces,
-                    mesh->bface, mesh->btag, o, H.mesh);
-    if (opt->face_switch) {
-      const size_t nif = H.mesh.if_K1.size();
-      o.face_switch.assign(opt->face_switch, opt->face_switch + nif);
-      cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces,
-                      mesh->bface, mesh->btag, o, H.mesh);
-    }
-    H.mono.init(mesh->dim, o.p);
-    H.np = H.mono.np;
-    H.vrule = cdg::simplex_rule(mesh->dim, 2 * o.p);
-    H.frule = cdg::simplex_rule(mesh->dim - 1, 2 * o.p);
-    H.lev.assign(1, cdg::Level());
-    double t1 = now();
-    cdg::build_level0(H);
-    double t2 = now();
-    cdg::agglomerate(H);
-    double t3 = now();
-    cdg::coarsen(H);
-    cdg::finalize_tree_order(H);
-    cdg::build_rhs_data(H);
-    double t4 = now();
-    H.t_mesh = t1 - t0;
-    H.t_assemble = t2 - t1;
-    H.t_agglomerate = t3 - t2;
-    H.t_coarsen = t4 - t3;
-  } catch (const std::invalid_argument& e) {
-    delete h;
-    return fail(nullptr, CDG_EINVAL, e.what());
-  } catch (const std::domain_error& e) {
-    delete h;
-    return fail(nullptr, CDG_EMESH, e.what());
-  } catch (const std::bad_alloc&) {
-    delete h;
-    return fail(nullptr, CDG_ENOMEM, "host allocation failed");
-  } catch (const std::exception& e) {
-    delete h;
-    return fail(nullptr, CDG_EMESH, e.what());
-  }
+  int rc = check_options(opt);
+  if (rc == CDG_OK) rc = check_mesh(mesh);
+  if (rc != CDG_OK) return rc;
+  cdg_handle* h = new cdg_handle();
+  h->opt = *opt;
+  h->opt.face_switch = nullptr;
+  h->opt.enumeration = nullptr;
+  h->opt.kappa = nullptr;
+  rc = guarded(h, [&] { build_one(mesh, opt, true, h->H); });
+  if (rc != CDG_OK) return rc;
   *out = h;
+  return CDG_OK;
+}
+
+int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_options* opt, cdg_handle** out) {
+  if (!out) return fail(nullptr, CDG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!meshes || !opt || n_meshes < 1) return fail(nullptr, CDG_EINVAL, "meshes, n_meshes or options invalid");
+  if (opt->kappa || opt->face_switch || opt->enumeration)
+    return fail(nullptr, CDG_EINVAL, "per-element arrays are not supported for batched handles");
+  int rc = check_options(opt);
+  for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
+  if (rc != CDG_OK) return rc;
+  cdg_handle* h = new cdg_handle();
+  h->opt = *opt;
+  rc = guarded(h, [&] {
+    std::vector<cdg::Hierarchy> subs(n_meshes);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t m = 0; m < n_meshes; ++m) {
+      try {
+        build_one(&meshes[m], opt, false, subs[m]);
+      } catch (...) {
+        subs[m].lev.clear();   // reported below
+      }
+    }
+    for (int32_t m = 0; m < n_meshes; ++m)
+      if (subs[m].lev.empty()) build_one(&meshes[m], opt, false, subs[m]);   // rethrows with the message
+    cdg::concat_hierarchies(subs, h->H);
+  });
+  if (rc != CDG_OK) return rc;
+  *out = h;
+  return CDG_OK;
+}
+
+int cdg_batch_offsets(const cdg_handle* h, int32_t* n_meshes, int64_t* elem_offsets, int64_t* bface_offsets) {
+  if (!h) return CDG_EINVAL;
+  const cdg::Hierarchy& H = h->H;
+  const int32_t nseg = (int32_t)H.seg_rows[0].size() - 1;
+  if (n_meshes) *n_meshes = nseg;
+  if (elem_offsets) {
+    if (H.subs.empty()) {
+      elem_offsets[0] = 0;
+      elem_offsets[1] = H.mesh.ne;
+    } else {
+      elem_offsets[0] = 0;
+      for (int32_t m = 0; m < nseg; ++m) elem_offsets[m + 1] = elem_offsets[m] + H.subs[m].mesh.ne;
+    }
+  }
+  if (bface_offsets)
+    for (int32_t m = 0; m <= nseg; ++m) bface_offsets[m] = H.seg_bface[m];
   return CDG_OK;
 }
 
@@ -167,38 +266,23 @@ int cdg_query(const cdg_handle* h, cdg_info* info) {
   info->setup_seconds[1] = H.t_assemble;
   info->setup_seconds[2] = H.t_agglomerate;
   info->setup_seconds[3] = H.t_coarsen;
+  info->n_meshes = (int32_t)H.seg_rows[0].size() - 1;
   return CDG_OK;
 }
 
 int cdg_quadrature_points(const cdg_handle* h, double* xq, double* xbq, int32_t* btag) {
   if (!h) return CDG_EINVAL;
   const cdg::Hierarchy& H = h->H;
-  const cdg::Mesh0& m = H.mesh;
-  const int d = m.d;
-  if (xq) {
-    const int nq = H.vrule.n();
-    for (int64_t K = 0; K < m.ne; ++K) {
-      const int64_t* ev = m.elem.data() + K * (d + 1);
-      for (int q = 0; q < nq; ++q)
-        for (int k = 0; k < d; ++k) {
-          double s = m.xyz[ev[0] * d + k];
-          for (int i = 0; i < d; ++i)
-            s += H.vrule.x[(size_t)q * d + i] * (m.xyz[ev[i + 1] * d + k] - m.xyz[ev[0] * d + k]);
-          xq[((size_t)K * nq + q) * d + k] = s;
-        }
-    }
+  if (H.subs.empty()) {
+    quad_points(H, xq, xbq, btag);
+    return CDG_OK;
   }
-  const int nfq = H.frule.n();
-  for (size_t b = 0; b < m.bf_K.size(); ++b) {
-    if (btag) btag[b] = m.bf_tag[b];
-    if (!xbq) continue;
-    const double* xv = &m.bf_xv[b * d * d];
-    for (int q = 0; q < nfq; ++q)
-      for (int k = 0; k < d; ++k) {
-        double s = xv[k];
-        for (int i = 0; i < d - 1; ++i) s += H.frule.x[(size_t)q * (d - 1) + i] * (xv[(i + 1) * d + k] - xv[k]);
-        xbq[((size_t)b * nfq + q) * d + k] = s;
-      }
+  const int d = H.mesh.d, nq = H.vrule.n(), nfq = H.frule.n();
+  size_t eo = 0, bo = 0;
+  for (const cdg::Hierarchy& S : H.subs) {
+    quad_points(S, xq ? xq + eo * nq * d : nullptr, xbq ? xbq + bo * nfq * d : nullptr, btag ? btag + bo : nullptr);
+    eo += S.mesh.ne;
+    bo += S.mesh.bf_K.size();
   }
   return CDG_OK;
 }
@@ -225,7 +309,7 @@ int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t*
 int cdg_export_agglomeration(const cdg_handle* h, int32_t level, int64_t* parent) {
   if (!h || !parent) return CDG_EINVAL;
   const cdg::Hierarchy& H = h->H;
-  if (level < 0 || level + 1 >= (int32_t)H.lev.size()) return CDG_EINVAL;
+  if (level < 0 || level + 1 >= (int32_t)H.lev.size() || H.lev[level].parent.empty()) return CDG_EINVAL;
   std::memcpy(parent, H.lev[level].parent.data(), sizeof(int64_t) * H.lev[level].n);
   return CDG_OK;
 }
@@ -243,18 +327,20 @@ int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN
 int cdg_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* u, int32_t use_u0,
               double* res_hist, int32_t* iters, int32_t host_pointers, void* stream) {
   if (!h || !f_q || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  int it = 0;
-  int rc = dev_solve(h, f_q, gD, gN, nullptr, u, use_u0, res_hist, &it, host_pointers, stream);
-  if (iters) *iters = it;
+  std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
+  int rc = dev_solve(h, f_q, gD, gN, nullptr, u, use_u0, res_hist, its.data(), host_pointers, stream);
+  if (iters)
+    for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
   return rc;
 }
 
 int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist, int32_t* iters,
                 void* stream) {
   if (!h || !b || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  int it = 0;
-  int rc = dev_solve(h, nullptr, nullptr, nullptr, b, u, use_u0, res_hist, &it, 0, stream);
-  if (iters) *iters = it;
+  std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
+  int rc = dev_solve(h, nullptr, nullptr, nullptr, b, u, use_u0, res_hist, its.data(), 0, stream);
+  if (iters)
+    for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
   return rc;
 }
 

@@ -29,7 +29,8 @@ constexpr int kMaxLev = CDG_MAX_LEVELS;
 constexpr int kThreads = 256;
 constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
 
-enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZOLD, S_TMP, S_FLAG = 15, S_COUNT = 16 };
+// per-segment CG scalars (one row of S_COUNT doubles per mesh of the handle)
+enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, S_FLAG = 15, S_COUNT = 16 };
 
 struct DevLevel {
   int n = 0;
@@ -87,9 +88,21 @@ struct DeviceState {
   float *r32 = nullptr, *z32 = nullptr;
   // staging for host-pointer solves
   double *f_stage = nullptr, *gD_stage = nullptr, *gN_stage = nullptr, *u_stage = nullptr;
-  double* scal = nullptr;
+  double* scal = nullptr;       // [nseg][S_COUNT]
   double* partial = nullptr;
   int npartial = 0;
+  // segments (meshes of a batched handle)
+  int nseg = 1, bps = 1;        // blocks per segment of the segmented vector kernels
+  long long* seg_dof = nullptr; // [nseg+1] level-0 dof offsets
+  int* crow_seg = nullptr;      // [nc] segment of each coarsest row
+  int* crow_off = nullptr;      // [nseg+1] coarsest row offsets
+  long long* cinv_off = nullptr;// [nseg+1] offsets of the dense inverses
+  std::vector<long long> h_seg_dof;
+  // private stream and the two captured graphs of a CG iteration
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr;
+  cudaGraphExec_t g1 = nullptr, g2 = nullptr;
+  long long g1_kernels = 0, g2_kernels = 0;
 };
 
 namespace {
@@ -162,7 +175,13 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
     L.bh = c.take<char>(nv * (l == 0 ? sizeof(double) : vsz));
   }
   D.nc = (int)(H.lev.back().n * np);
-  D.coarse_inv = c.take<double>((size_t)D.nc * D.nc);
+  D.nseg = (int)H.seg_rows[0].size() - 1;
+  D.bps = std::max(1, kDotBlocks / D.nseg);
+  D.seg_dof = c.take<long long>(D.nseg + 1);
+  D.crow_seg = c.take<int>(D.nc);
+  D.crow_off = c.take<int>(D.nseg + 1);
+  D.cinv_off = c.take<long long>(D.nseg + 1);
+  D.coarse_inv = c.take<double>(H.coarse_inv.size());
   D.coarse_b = c.take<double>(D.nc);
   D.coarse_x = c.take<double>(D.nc);
   D.rhs_vol = c.take<double>(H.rhs_vol.size());
@@ -191,8 +210,8 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
   D.gD_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
   D.gN_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
   D.u_stage = c.take<double>(vecbytes_elems);
-  D.scal = c.take<double>(S_COUNT);
-  D.npartial = std::max<int>(kDotBlocks, (int)((int64_t)ne * np / 64 + 2));
+  D.scal = c.take<double>((size_t)S_COUNT * D.nseg);
+  D.npartial = std::max<int>(std::max(kDotBlocks, D.nseg * D.bps), (int)((int64_t)ne * np / 64 + 2));
   D.partial = c.take<double>((size_t)D.npartial * 2);
   return (c.off + 255) & ~size_t(255);
 }
@@ -361,16 +380,21 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(int n, const int* __r
   x[row] = ADD ? x[row] + s : s;
 }
 
-// dense symmetric inverse times vector, one warp per row: x[i] = sum_j Ainv[i][j] b[j] (FP64)
+// coarsest solve: x = Ainv_m b on every segment m, one warp per row; each
+// segment has its own dense inverse (row-major, n_m x n_m), FP64 accumulation
 template <typename TI, typename TO>
-__global__ void coarse_kernel(int nc, const double* __restrict__ Ainv, const TI* __restrict__ b,
-                              TO* __restrict__ x) {
+__global__ void coarse_kernel(int nc, const int* __restrict__ crow_seg, const int* __restrict__ crow_off,
+                              const long long* __restrict__ cinv_off, const double* __restrict__ Ainv,
+                              const TI* __restrict__ b, TO* __restrict__ x) {
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= nc) return;
-  const double* a = Ainv + (size_t)row * nc;
+  const int m = crow_seg[row];
+  const int r0 = crow_off[m], nm = crow_off[m + 1] - r0;
+  const double* a = Ainv + cinv_off[m] + (size_t)(row - r0) * nm;
+  const TI* bm = b + r0;
   double s = 0.0;
-  for (int j = lane; j < nc; j += 32) s = fma(a[j], (double)b[j], s);
+  for (int j = lane; j < nm; j += 32) s = fma(a[j], (double)bm[j], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (TO)s;
 }
@@ -393,12 +417,27 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
-// partial[blk] = sum x.y (and partial[npart + blk] = sum x.w when w != nullptr)
-__global__ void __launch_bounds__(kThreads) dot_kernel(size_t n, const double* __restrict__ x,
-                                                       const double* __restrict__ y, const double* __restrict__ w,
-                                                       double* __restrict__ partial, int npart) {
+// Segmented vector kernels: block seg * bps + c handles chunk c of segment
+// seg (the level-0 dofs of one mesh), so every block has one set of scalars.
+__device__ __forceinline__ void seg_range(const long long* __restrict__ seg_dof, int bps, int& seg, size_t& lo,
+                                          size_t& hi) {
+  seg = blockIdx.x / bps;
+  const int c = blockIdx.x - seg * bps;
+  const size_t a = (size_t)seg_dof[seg], len = (size_t)seg_dof[seg + 1] - a;
+  lo = a + len * c / bps;
+  hi = a + len * (c + 1) / bps;
+}
+
+// partial[blk] = sum x.y over the block's chunk (and partial[npart + blk] = sum x.w)
+__global__ void __launch_bounds__(kThreads) dot_kernel(const long long* __restrict__ seg_dof, int bps,
+                                                       const double* __restrict__ x, const double* __restrict__ y,
+                                                       const double* __restrict__ w, double* __restrict__ partial,
+                                                       int npart) {
+  int seg;
+  size_t lo, hi;
+  seg_range(seg_dof, bps, seg, lo, hi);
   double s = 0.0, s2 = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     s = fma(x[i], y[i], s);
     if (w) s2 = fma(x[i], w[i], s2);
   }
@@ -410,16 +449,20 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(size_t n, const double* _
   }
 }
 
-// Sums partials in a fixed order and updates the CG scalars.
-// which: 0 -> PQ (alpha = RZ/PQ), 1 -> RR, 2 -> RZ (beta, Fletcher-Reeves or,
-// when flexible, Polak-Ribiere with the second partial = (r_new, z_old)), 3 -> BB
-__global__ void finalize_kernel(const double* __restrict__ partial, int cnt, int npart, int which,
-                                int flexible, double* __restrict__ scal) {
+// One block per segment: sums its cnt partials in a fixed order and updates the
+// segment's CG scalars.  which: 0 PQ (alpha; breakdown if p.Ap <= 0), 1 RR
+// (iteration count, convergence ||r|| <= tol ||b||), 2 RZ (beta: Fletcher-Reeves,
+// or Polak-Ribiere with the second partial (r_new, z_old) when flexible),
+// 3 BB, 4 initial RR.  A segment marked done gets alpha = beta = 0.
+__global__ void finalize_kernel(const double* __restrict__ partial, int cnt, int npart, int which, int flexible,
+                                double tol, double* __restrict__ scal) {
   __shared__ double red[kThreads / 32];
+  const int m = blockIdx.x;
+  const double* pm = partial + (size_t)m * cnt;
   double s = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    s += partial[i];
-    if (which == 2 && flexible) s2 += partial[npart + i];
+    s += pm[i];
+    if (which == 2 && flexible) s2 += partial[npart + (size_t)m * cnt + i];
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -434,29 +477,49 @@ __global__ void finalize_kernel(const double* __restrict__ partial, int cnt, int
   if (threadIdx.x == 0) {
     double tot2 = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) tot2 += red[w];
+    double* sc = scal + (size_t)m * S_COUNT;
+    const bool done = sc[S_DONE] != 0.0;
     if (which == 0) {
-      scal[S_PQ] = tot;
-      scal[S_ALPHA] = scal[S_RZ] / tot;
-    } else if (which == 1) {
-      scal[S_RR] = tot;
+      sc[S_PQ] = tot;
+      if (!done && !(tot > 0.0)) {
+        sc[S_BREAK] = 1.0;
+        sc[S_DONE] = 1.0;
+      }
+      sc[S_ALPHA] = sc[S_DONE] != 0.0 ? 0.0 : sc[S_RZ] / tot;
+    } else if (which == 1 || which == 4) {
+      if (!done) {
+        sc[S_RR] = tot;
+        if (which == 1) sc[S_IT] += 1.0;
+        if (!isfinite(tot)) {
+          sc[S_BREAK] = 1.0;
+          sc[S_DONE] = 1.0;
+        } else if (sqrt(tot) <= tol * sqrt(sc[S_BB])) {
+          sc[S_DONE] = 1.0;
+        }
+      }
     } else if (which == 2) {
-      const double rz_old = scal[S_RZ];
-      scal[S_BETA] = flexible ? (tot - tot2) / rz_old : tot / rz_old;
-      scal[S_RZ] = tot;
+      const double rz_old = sc[S_RZ];
+      sc[S_BETA] = done ? 0.0 : (flexible ? (tot - tot2) / rz_old : tot / rz_old);
+      sc[S_RZ] = tot;
     } else {
-      scal[S_BB] = tot;
+      sc[S_BB] = tot;
+      if (!(tot > 0.0)) sc[S_DONE] = 1.0;
     }
   }
 }
 
-// x += alpha p; r -= alpha q; partial of r.r
-__global__ void __launch_bounds__(kThreads) cg_update_kernel(size_t n, const double* __restrict__ scal,
+// x += alpha p; r -= alpha q; partial of r.r (per segment chunk)
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(const long long* __restrict__ seg_dof, int bps,
+                                                             const double* __restrict__ scal,
                                                              const double* __restrict__ p,
                                                              const double* __restrict__ q, double* __restrict__ x,
                                                              double* __restrict__ r, double* __restrict__ partial) {
-  const double alpha = scal[S_ALPHA];
+  int seg;
+  size_t lo, hi;
+  seg_range(seg_dof, bps, seg, lo, hi);
+  const double alpha = scal[(size_t)seg * S_COUNT + S_ALPHA];
   double s = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -466,12 +529,15 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(size_t n, const dou
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// p = z + beta p (beta = 0: p = z)
-__global__ void __launch_bounds__(kThreads) cg_p_kernel(size_t n, const double* __restrict__ scal, int first,
+// p = z + beta p (first: p = z)
+__global__ void __launch_bounds__(kThreads) cg_p_kernel(const long long* __restrict__ seg_dof, int bps,
+                                                        const double* __restrict__ scal, int first,
                                                         const double* __restrict__ z, double* __restrict__ p) {
-  const double beta = first ? 0.0 : scal[S_BETA];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+  int seg;
+  size_t lo, hi;
+  seg_range(seg_dof, bps, seg, lo, hi);
+  const double beta = first ? 0.0 : scal[(size_t)seg * S_COUNT + S_BETA];
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = first ? z[i] : fma(beta, p[i], z[i]);
 }
 
 // b (tree order, or user order) from f at volume points and g_D / g_N at boundary points
@@ -725,7 +791,8 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   const int nlev = D.nlev;
   const double w = o.omega;
   if (nlev == 1) {
-    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, b0, z0);
+    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off,
+           D.coarse_inv, b0, z0);
     return true;
   }
   std::vector<const T*> bl(nlev);
@@ -762,7 +829,8 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   // coarsest
   {
     const DevLevel& C = D.lev[nlev - 1];
-    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, (const T*)C.b, (T*)C.x);
+    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off,
+           D.coarse_inv, (const T*)C.b, (T*)C.x);
   }
   // upward sweep
   for (int l = nlev - 2; l >= 0; --l) {
@@ -813,10 +881,10 @@ int precond(cdg_handle* h, const double* r, double* z, cudaStream_t s) {
 
 int dot_to(cdg_handle* h, const double* x, const double* y, const double* w, int which, cudaStream_t s) {
   DeviceState& D = *h->dev;
-  const size_t n = (size_t)D.ndofs;
-  const unsigned g = vec_grid(n);
-  launch(dot_kernel, g, kThreads, s, n, x, y, w, D.partial, D.npartial);
-  launch(finalize_kernel, 1, kThreads, s, D.partial, (int)g, D.npartial, which, w != nullptr, D.scal);
+  const unsigned g = (unsigned)(D.nseg * D.bps);
+  launch(dot_kernel, g, kThreads, s, (const long long*)D.seg_dof, D.bps, x, y, w, D.partial, D.npartial);
+  launch(finalize_kernel, (unsigned)D.nseg, kThreads, s, (const double*)D.partial, D.bps, D.npartial, which,
+         w != nullptr ? 1 : 0, h->opt.tol, D.scal);
   CDG_CHECK_LAUNCH(h, "dot");
   return CDG_OK;
 }
@@ -910,6 +978,16 @@ int dev_bytes(const cdg_handle* h, int64_t* bytes) {
 }
 
 void dev_release(cdg_handle* h) {
+  if (h->dev) {
+    DeviceState& D = *h->dev;
+    if (D.g1) cudaGraphExecDestroy(D.g1);
+    if (D.g2) cudaGraphExecDestroy(D.g2);
+    if (D.stream) {
+      cudaStreamSynchronize(D.stream);
+      cudaStreamDestroy(D.stream);
+    }
+    if (D.ev_in) cudaEventDestroy(D.ev_in);
+  }
   delete h->dev;
   h->dev = nullptr;
 }
@@ -925,7 +1003,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
     h->err = "device buffer must be 256-byte aligned";
     return CDG_EINVAL;
   }
-  delete h->dev;
+  dev_release(h);
   h->dev = new DeviceState();
   DeviceState& D = *h->dev;
   D.base = (char*)buf;
@@ -957,6 +1035,25 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
     cudaStreamSynchronize(s);
   }
   upload(D.coarse_inv, H.coarse_inv, s);
+  {
+    std::vector<long long> sd(D.nseg + 1), co(D.nseg + 1);
+    std::vector<int> cro(D.nseg + 1), crs(D.nc);
+    const std::vector<cdg::i64>& r0 = H.seg_rows[0];
+    const std::vector<cdg::i64>& rc = H.seg_rows[D.nlev - 1];
+    for (int m = 0; m <= D.nseg; ++m) {
+      sd[m] = (long long)r0[m] * D.np;
+      cro[m] = (int)(rc[m] * D.np);
+      co[m] = (long long)H.seg_coarse[m];
+    }
+    for (int m = 0; m < D.nseg; ++m)
+      for (int r = cro[m]; r < cro[m + 1]; ++r) crs[r] = m;
+    D.h_seg_dof = sd;
+    upload(D.seg_dof, sd, s);
+    upload(D.crow_off, cro, s);
+    upload(D.cinv_off, co, s);
+    upload(D.crow_seg, crs, s);
+    cudaStreamSynchronize(s);
+  }
   upload(D.rhs_vol, H.rhs_vol, s);
   upload(D.rhs_bptr, to_i32(H.rhs_bptr), s);
   upload(D.rhs_bface, to_i32(H.rhs_bface), s);
@@ -968,8 +1065,10 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   upload(D.dk_nbr, to_i32(H.dk_nbr), s);
   upload(D.dk_blk, H.dk_blk, s);
   upload(D.kappa, H.kappa_w, s);
-  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT, s);
+  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT * D.nseg, s);
   cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D.ev_in, cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
@@ -1009,7 +1108,8 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   DeviceState& D = *h->dev;
   cudaStream_t s = (cudaStream_t)stream;
   if (op == 5) {
-    launch(coarse_kernel<double, double>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.coarse_inv, x, y);
+    launch(coarse_kernel<double, double>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off,
+           D.cinv_off, D.coarse_inv, x, y);
     CDG_CHECK_LAUNCH(h, "coarse");
     return CDG_OK;
   }
@@ -1054,18 +1154,88 @@ int dev_vcycle(cdg_handle* h, const double* r, double* z, void* stream) {
   return precond(h, r, z, (cudaStream_t)stream);
 }
 
+// One CG iteration is split in two captured graphs: G1 = [q = A p, p.q, x and r
+// updates, r.r] and G2 = [z = V(r), r.z, p = z + beta p].  The host reads the
+// per-segment scalars between them (convergence of every mesh is decided on the
+// device; converged meshes get alpha = beta = 0).
+static int cg_part1(cdg_handle* h, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  const DevLevel& L0 = D.lev[0];
+  const unsigned gseg = (unsigned)(D.nseg * D.bps);
+  if (D.nseg == 1) {
+    const unsigned g = rows_grid(L0.n, D.np);
+    launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, h->opt.omega,
+                       D.partial, s, D.scal + S_FLAG);
+    launch(finalize_kernel, 1u, kThreads, s, (const double*)D.partial, (int)g, D.npartial, 0, 0, h->opt.tol,
+           D.scal);
+  } else {
+    launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, h->opt.omega,
+                       (double*)nullptr, s, D.scal + S_FLAG);
+    int rc = dot_to(h, D.p, D.q, nullptr, 0, s);
+    if (rc != CDG_OK) return rc;
+  }
+  launch(cg_update_kernel, gseg, kThreads, s, (const long long*)D.seg_dof, D.bps, (const double*)D.scal,
+         (const double*)D.p, (const double*)D.q, D.x, D.r, D.partial);
+  launch(finalize_kernel, (unsigned)D.nseg, kThreads, s, (const double*)D.partial, D.bps, D.npartial, 1, 0,
+         h->opt.tol, D.scal);
+  CDG_CHECK_LAUNCH(h, "cg");
+  return CDG_OK;
+}
+
+static int cg_part2(cdg_handle* h, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  const bool flexible = D.precision != 0;
+  const size_t n = (size_t)D.ndofs;
+  if (flexible) cudaMemcpyAsync(D.zold, D.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  int rc = precond(h, D.r, D.z, s);
+  if (rc != CDG_OK) return rc;
+  if ((rc = dot_to(h, D.r, D.z, flexible ? D.zold : nullptr, 2, s)) != CDG_OK) return rc;
+  launch(cg_p_kernel, (unsigned)(D.nseg * D.bps), kThreads, s, (const long long*)D.seg_dof, D.bps,
+         (const double*)D.scal, 0, (const double*)D.z, D.p);
+  CDG_CHECK_LAUNCH(h, "cg");
+  return CDG_OK;
+}
+
+// Captures one part into an executable graph on the private stream.
+static int capture(cdg_handle* h, int (*part)(cdg_handle*, cudaStream_t), cudaGraphExec_t* exec,
+                   long long* kernels) {
+  DeviceState& D = *h->dev;
+  cudaGraph_t g = nullptr;
+  const long long before = g_launches.load();
+  cudaError_t e = cudaStreamBeginCapture(D.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+  const int rc = part(h, D.stream);
+  e = cudaStreamEndCapture(D.stream, &g);
+  // captured launches run when the graph is launched: count them there
+  *kernels = g_launches.load() - before;
+  g_launches.fetch_sub(*kernels, std::memory_order_relaxed);
+  if (rc != CDG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  return CDG_OK;
+}
+
 int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, const double* b_user, double* u,
               int use_u0, double* res_hist, int* iters, int host_ptrs, void* stream) {
-  *iters = 0;
   if (!h->dev) {
     h->err = "cdg_bind_device has not been called";
     return CDG_ESTATE;
   }
   DeviceState& D = *h->dev;
-  cudaStream_t s = (cudaStream_t)stream;
+  const int nseg = D.nseg;
+  for (int m = 0; m < nseg; ++m) iters[m] = 0;
+  // all work on the private stream, ordered after the caller's stream
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaStream_t s = D.stream;
+  cudaEventRecord(D.ev_in, cs);
+  cudaStreamWaitEvent(s, D.ev_in, 0);
   const cdg_options& o = h->opt;
   const size_t n = (size_t)D.ndofs;
-  const bool flexible = D.precision != 0;
   double* u_dev = u;
   int rc;
   if (host_ptrs) {
@@ -1078,7 +1248,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     gN = gN ? D.gN_stage : nullptr;
     u_dev = D.u_stage;
   }
-  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT, s);   // scalars and the wait-timeout flag
+  cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT * nseg, s);   // scalars and the wait-timeout flag
   // right-hand side in tree order
   if (b_user) {
     launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
@@ -1095,58 +1265,65 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     cudaMemcpyAsync(D.r, D.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   }
   if ((rc = dot_to(h, D.bt, D.bt, nullptr, 3, s)) != CDG_OK) return rc;
-  if ((rc = dot_to(h, D.r, D.r, nullptr, 1, s)) != CDG_OK) return rc;
-  double hs[S_COUNT];
-  cudaMemcpyAsync(hs, D.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if ((rc = dot_to(h, D.r, D.r, nullptr, 4, s)) != CDG_OK) return rc;
+  std::vector<double> hs((size_t)S_COUNT * nseg);
+  cudaMemcpyAsync(hs.data(), D.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve init");
-  const double bnorm = std::sqrt(hs[S_BB]);
+  const int stride = o.maxit + 1;
+  auto rel = [&](int m) {
+    const double* sc = &hs[(size_t)m * S_COUNT];
+    return sc[S_BB] > 0.0 ? std::sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
+  };
+  std::vector<char> done(nseg, 0);
+  int ndone = 0;
+  for (int m = 0; m < nseg; ++m) {
+    if (res_hist) res_hist[(size_t)m * stride] = rel(m);
+    if (hs[(size_t)m * S_COUNT + S_DONE] != 0.0) {
+      done[m] = 1;
+      ++ndone;
+    }
+  }
   int status = CDG_OK;
   int it = 0;
-  auto rel = [&](double rr) { return bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0; };
-  if (res_hist) res_hist[0] = rel(hs[S_RR]);
-  if (bnorm == 0.0) {
-    cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
-  } else if (rel(hs[S_RR]) > o.tol) {
+  if (ndone < nseg) {
     if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
     if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
-    launch(cg_p_kernel, vec_grid(n), kThreads, s, n, D.scal, 1, D.z, D.p);
+    launch(cg_p_kernel, (unsigned)(nseg * D.bps), kThreads, s, (const long long*)D.seg_dof, D.bps,
+           (const double*)D.scal, 1, (const double*)D.z, D.p);
+    if (!D.g1 && (rc = capture(h, cg_part1, &D.g1, &D.g1_kernels)) != CDG_OK) return rc;
+    if (!D.g2 && (rc = capture(h, cg_part2, &D.g2, &D.g2_kernels)) != CDG_OK) return rc;
     while (true) {
       if (it >= o.maxit) {
         status = CDG_ENOCONV;
         break;
       }
-      // q = A p and p.q
-      const unsigned g = rows_grid(L0.n, D.np);
-      launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, o.omega,
-                         D.partial, s, D.scal + S_FLAG);
-      launch(finalize_kernel, 1, kThreads, s, D.partial, (int)g, D.npartial, 0, 0, D.scal);
-      const unsigned gv = vec_grid(n);
-      launch(cg_update_kernel, gv, kThreads, s, n, D.scal, D.p, D.q, D.x, D.r, D.partial);
-      launch(finalize_kernel, 1, kThreads, s, D.partial, (int)gv, D.npartial, 1, 0, D.scal);
-      CDG_CHECK_LAUNCH(h, "cg");
-      cudaMemcpyAsync(hs, D.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+      e = cudaGraphLaunch(D.g1, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+      cudaMemcpyAsync(hs.data(), D.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_fail(h, e, "cg");
+      g_launches.fetch_add(D.g1_kernels, std::memory_order_relaxed);
       ++it;
-      const double rr = rel(hs[S_RR]);
-      if (res_hist) res_hist[it] = rr;
-      if (hs[S_FLAG] != 0.0) {
-        status = CDG_ETIMEOUT;
-        h->err = "a bounded wait on a bulk copy into shared memory expired";
-        break;
+      for (int m = 0; m < nseg; ++m) {
+        if (done[m]) continue;
+        const double* sc = &hs[(size_t)m * S_COUNT];
+        iters[m] = it;
+        if (res_hist) res_hist[(size_t)m * stride + it] = rel(m);
+        if (sc[S_DONE] != 0.0) {
+          done[m] = 1;
+          ++ndone;
+          if (sc[S_BREAK] != 0.0) {
+            status = CDG_EBREAKDOWN;
+            h->err = "CG breakdown on mesh " + std::to_string(m) + " at iteration " + std::to_string(it) +
+                     ": p^T A p = " + std::to_string(sc[S_PQ]) + ", ||r||^2 = " + std::to_string(sc[S_RR]);
+          }
+        }
       }
-      if (!(hs[S_PQ] > 0.0) || !std::isfinite(rr)) {
-        status = CDG_EBREAKDOWN;
-        h->err = "CG breakdown at iteration " + std::to_string(it) + ": p^T A p = " + std::to_string(hs[S_PQ]) +
-                 ", (r, z) = " + std::to_string(hs[S_RZ]) + ", ||r||/||b|| = " + std::to_string(rr);
-        break;
-      }
-      if (rr <= o.tol) break;
-      if (flexible) cudaMemcpyAsync(D.zold, D.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-      if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
-      if ((rc = dot_to(h, D.r, D.z, flexible ? D.zold : nullptr, 2, s)) != CDG_OK) return rc;
-      launch(cg_p_kernel, vec_grid(n), kThreads, s, n, D.scal, 0, D.z, D.p);
+      if (ndone == nseg) break;
+      e = cudaGraphLaunch(D.g2, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+      g_launches.fetch_add(D.g2_kernels, std::memory_order_relaxed);
     }
   }
   launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, D.x, u_dev, 0);
@@ -1154,8 +1331,11 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve end");
   CDG_CHECK_LAUNCH(h, "solve end");
-  *iters = it;
-  if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
+  if (status == CDG_ENOCONV) {
+    for (int m = 0; m < nseg; ++m)
+      if (!done[m]) iters[m] = it;
+    h->err = "maximum number of iterations reached";
+  }
   return status;
 }
 

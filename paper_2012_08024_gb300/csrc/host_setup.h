@@ -134,9 +134,18 @@ struct Hierarchy {
   std::vector<i64> dk_nbr;                    // neighbour J of each q-face
   std::vector<double> dk_blk;                 // [nq_faces][3][np][np]: KJ, JK, JJ
   std::vector<double> kappa_w;                // kappa per element (working order), 1 if none
+  // segments: independent meshes of a batched handle (one segment otherwise)
+  std::vector<std::vector<i64>> seg_rows;     // [level][nseg+1] first tree row of each segment
+  std::vector<i64> seg_coarse;                // [nseg+1] offsets of each dense inverse in coarse_inv
+  std::vector<i64> seg_bface;                 // [nseg+1] first boundary face of each segment
+  std::vector<Hierarchy> subs;                // per-mesh set-ups of a batched handle (mesh data only)
   // timings
   double t_mesh = 0, t_assemble = 0, t_agglomerate = 0, t_coarsen = 0;
 };
+
+// Concatenates finalized per-mesh hierarchies (same dim, p and level count)
+// into one block-diagonal hierarchy with one segment per mesh.
+void concat_hierarchies(std::vector<Hierarchy>& subs, Hierarchy& B);
 
 // stage functions (each throws std::runtime_error with a message on bad input)
 void build_mesh(const int dim, i64 nv, const double* xyz, i64 ne, const i64* elem, i64 nbf,

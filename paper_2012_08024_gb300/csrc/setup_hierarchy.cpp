@@ -501,6 +501,9 @@ void finalize_tree_order(Hierarchy& H) {
       for (i64 a = 0; a < H.lev[l + 1].n; ++a) cp[a + 1] += cp[a];
     }
   }
+  H.seg_rows.assign(nlev, {});
+  for (int l = 0; l < nlev; ++l) H.seg_rows[l] = {0, H.lev[l].n};
+  H.seg_bface = {0, (i64)H.mesh.bf_K.size()};
   // coarsest: dense SPD inverse
   const Level& Cl = H.lev.back();
   const i64 nc = Cl.n * np;
@@ -516,6 +519,7 @@ void finalize_tree_order(Hierarchy& H) {
   if (!spd_inverse((int)nc, dense.data(), H.coarse_inv.data()) &&
       !lu_inverse((int)nc, dense.data(), H.coarse_inv.data()))
     throw std::runtime_error("singular coarsest operator");
+  H.seg_coarse = {0, (i64)H.coarse_inv.size()};
 }
 
 void build_rhs_data(Hierarchy& H) {
