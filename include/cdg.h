@@ -74,7 +74,8 @@ typedef struct {
   double omega;             /* block-Jacobi damping, default 2/3 (Section 4.3) */
   int32_t max_levels;       /* levels including level 0 (Algorithm 1 stops earlier at 1 element) */
   uint64_t seed;            /* tie-break seed of Algorithm 2 */
-  int32_t precision;        /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 CG */
+  int32_t precision;        /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 CG;
+                               2: BF16 V-cycle blocks (FP32 arithmetic) for cdg_solve_multi */
   int32_t switch_kind;      /* 0: directional consistent switch, 1: natural switch (Section 2.2) */
   const int8_t* face_switch;   /* nullable: S_{K1}^{K2} per interior face (library face order) */
   const int64_t* enumeration;  /* nullable: element enumeration N(K) of the natural switch */
@@ -82,6 +83,7 @@ typedef struct {
   int32_t coarsen;          /* 0: flux coarsening (Section 4.1), 1: primal A_{l+1} = R A_l L */
   double tol;               /* relative residual ||r||/||b|| to stop CG, default 1e-10 */
   int32_t maxit;            /* CG iteration limit, default 500 */
+  int32_t nrhs;             /* columns of cdg_solve_multi (0 = none), at most 1024 */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16
@@ -167,6 +169,15 @@ int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD_q, const double* 
  * CDG_EBREAKDOWN, CDG_ECUDA. */
 int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double* gN_q, double* u,
               int32_t use_u0, double* res_hist, int32_t* iters, int32_t host_pointers, void* stream);
+
+/* Many right-hand sides on one mesh (handle created with nrhs = R > 0; not for
+ * batched handles): solves A_0 u_r = b(f_r) for r < R in one CG with per-column
+ * scalars.  f_q [R][n_elements][nq] device (zero boundary data), u
+ * [R][n_elements][n_p] device, res_hist [R][maxit+1] and iters [R] host.
+ * Vectors are stored [element][n_p][R] on the device so every operator block
+ * is read once per R columns; the V-cycle uses FP32 (precision 1) or BF16
+ * (precision 2) block copies with FP32 arithmetic, the outer CG is FP64. */
+int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int32_t* iters, void* stream);
 
 /* Same solve from a given load vector b (device, user order, [n_elements][n_p]). */
 int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist,

@@ -38,7 +38,7 @@ class cdg_options(C.Structure):
                 ("omega", C.c_double), ("max_levels", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
-                ("tol", C.c_double), ("maxit", C.c_int32)]
+                ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -81,6 +81,7 @@ SIGNATURES = {
     "cdg_kernel_launches": (_I64, []),
     "cdg_smooth_static": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "cdg_solve_adjoint": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "cdg_solve_multi": (_I32, [_P, _P, _P, _P, _P, _P]),
     "cdg_rhs_adjoint": (_I32, [_P, _P, _P, _P]),
     "cdg_kappa_gradient": (_I32, [_P, _P, _P, _P, _P, _P]),
 }
@@ -121,7 +122,7 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 COARSEN = {"flux": 0, "primal": 1}
 
 
@@ -131,9 +132,10 @@ class Solver:
     def __init__(self, mesh, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
-                 coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500):
+                 coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0):
         L = lib()
         self._keep = []
+        self.nrhs = nrhs
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         elem = np.ascontiguousarray(mesh.elem, dtype=np.int64)
         bface = np.ascontiguousarray(mesh.bface, dtype=np.int64).reshape(-1, mesh.dim)
@@ -147,6 +149,7 @@ class Solver:
         o.max_levels, o.seed = max_levels, seed
         o.precision, o.switch_kind = PRECISION[precision], switch_kind
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
+        o.nrhs = nrhs
         arrs = {}
         if face_switch is not None:
             arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)
@@ -257,6 +260,20 @@ class Solver:
         if rc not in (0, 3):
             self._check(rc)
         return u, hist[:it.value + 1], it.value, rc
+
+    def solve_multi(self, f_q, stream=None):
+        """f_q [R][n_elements][nq] device -> u [R][n_elements][n_p], per-column
+        residual histories, iteration counts, status."""
+        import torch
+        R = self.nrhs
+        u = torch.empty((R, self.ne, self.np_), dtype=torch.float64, device=f_q.device)
+        hist = np.zeros((R, self.maxit + 1))
+        its = np.zeros(R, dtype=np.int32)
+        rc = lib().cdg_solve_multi(self._h, _ptr(f_q.contiguous()), _ptr(u), hist.ctypes.data, its.ctypes.data,
+                                   _stream_ptr(stream))
+        if rc not in (0, 3):
+            self._check(rc)
+        return u, [hist[r, :its[r] + 1] for r in range(R)], its, rc
 
     def solve_adjoint(self, dLdu, stream=None):
         import torch

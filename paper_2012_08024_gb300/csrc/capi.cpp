@@ -31,7 +31,10 @@ static int check_options(const cdg_options* opt) {
     return fail(nullptr, CDG_EINVAL, "need nu_pre, nu_post >= 0 and at least one smoothing step");
   if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0))
     return fail(nullptr, CDG_EINVAL, "bad omega, gamma, tol or maxit");
-  if (opt->precision < 0 || opt->precision > 1) return fail(nullptr, CDG_EINVAL, "precision must be 0 or 1");
+  if (opt->precision < 0 || opt->precision > 2) return fail(nullptr, CDG_EINVAL, "precision must be 0, 1 or 2");
+  if (opt->nrhs < 0 || opt->nrhs > 1024) return fail(nullptr, CDG_EINVAL, "nrhs must be in [0, 1024]");
+  if (opt->precision == 2 && opt->nrhs == 0)
+    return fail(nullptr, CDG_EINVAL, "precision 2 (BF16 blocks) is the multi-right-hand-side mode: set nrhs");
   return CDG_OK;
 }
 
@@ -188,8 +191,8 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
   if (!out) return fail(nullptr, CDG_EINVAL, "out is NULL");
   *out = nullptr;
   if (!meshes || !opt || n_meshes < 1) return fail(nullptr, CDG_EINVAL, "meshes, n_meshes or options invalid");
-  if (opt->kappa || opt->face_switch || opt->enumeration)
-    return fail(nullptr, CDG_EINVAL, "per-element arrays are not supported for batched handles");
+  if (opt->kappa || opt->face_switch || opt->enumeration || opt->nrhs)
+    return fail(nullptr, CDG_EINVAL, "per-element arrays and nrhs are not supported for batched handles");
   int rc = check_options(opt);
   for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
   if (rc != CDG_OK) return rc;
@@ -372,6 +375,15 @@ int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream) {
 
 int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
   return dev_smooth_static(h, level, x, b, y, stream);
+}
+
+int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int32_t* iters, void* stream) {
+  if (!h || !f_q || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  std::vector<int> its(h->opt.nrhs > 0 ? h->opt.nrhs : 1, 0);
+  const int rc = dev_solve_multi(h, f_q, u, res_hist, its.data(), stream);
+  if (iters)
+    for (size_t r = 0; r < its.size() && h->opt.nrhs > 0; ++r) iters[r] = its[r];
+  return rc;
 }
 
 int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,

@@ -16,94 +16,14 @@
 #include <string>
 #include <vector>
 
-#include "handle.h"
+#include "device_state.h"
 
 #include <atomic>
 #include <mutex>
 
 static std::atomic<long long> g_launches{0};
-
-namespace {
-
-constexpr int kMaxLev = CDG_MAX_LEVELS;
-constexpr int kThreads = 256;
-constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
-
-// per-segment CG scalars (one row of S_COUNT doubles per mesh of the handle)
-enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, S_FLAG = 15, S_COUNT = 16 };
-
-struct DevLevel {
-  int n = 0;
-  int64_t nnzb = 0;
-  int* rowptr = nullptr;
-  int* col = nullptr;
-  double* A = nullptr;
-  double* Dinv = nullptr;
-  double* L = nullptr;
-  int* parent = nullptr;
-  int* childptr = nullptr;   // children range of each element of this level (l >= 1)
-  float* A32 = nullptr;
-  float* Dinv32 = nullptr;
-  float* L32 = nullptr;
-  int* hrowptr = nullptr;    // Ahat = D^{-1}(A - D): row-scaled off-diagonal blocks (smoother)
-  int* hcol = nullptr;
-  double* Ahat = nullptr;
-  float* Ahat32 = nullptr;
-  int64_t hnnzb = 0;
-  void* bh = nullptr;        // D^{-1} b of the current V-cycle visit
-  void* x = nullptr;         // V-cycle work vectors in the V-cycle precision
-  void* t = nullptr;
-  void* r = nullptr;
-  void* b = nullptr;
-};
-
-}  // namespace
-
-struct DeviceState {
-  char* base = nullptr;
-  int64_t bytes = 0;
-  int nlev = 0, np = 0, d = 0, nq = 0, nfq = 0, precision = 0;
-  int64_t ne = 0, ndofs = 0, nbf = 0;
-  DevLevel lev[kMaxLev];
-  double* coarse_inv = nullptr;
-  int nc = 0;
-  double* coarse_b = nullptr;   // FP64 staging of the coarsest right-hand side / solution
-  double* coarse_x = nullptr;
-  // rhs data
-  double* rhs_vol = nullptr;
-  int* rhs_bptr = nullptr;
-  int* rhs_bface = nullptr;
-  double* rhs_bdata = nullptr;
-  int* btag = nullptr;
-  int* perm0 = nullptr;         // tree row -> user element
-  // d A_0 / d kappa pieces (tree order)
-  double* dk_own = nullptr;
-  int* dk_ptr = nullptr;
-  int* dk_nbr = nullptr;
-  double* dk_blk = nullptr;
-  double* kappa = nullptr;
-  // CG vectors (FP64, tree order)
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr,
-         *zold = nullptr;
-  float *r32 = nullptr, *z32 = nullptr;
-  // staging for host-pointer solves
-  double *f_stage = nullptr, *gD_stage = nullptr, *gN_stage = nullptr, *u_stage = nullptr;
-  double* scal = nullptr;       // [nseg][S_COUNT]
-  double* partial = nullptr;
-  int npartial = 0;
-  // segments (meshes of a batched handle)
-  int nseg = 1, bps = 1;        // blocks per segment of the segmented vector kernels
-  long long* seg_dof = nullptr; // [nseg+1] level-0 dof offsets
-  int* crow_seg = nullptr;      // [nc] segment of each coarsest row
-  int* crow_off = nullptr;      // [nseg+1] coarsest row offsets
-  long long* cinv_off = nullptr;// [nseg+1] offsets of the dense inverses
-  std::vector<long long> h_seg_dof;
-  // private stream and the two captured graphs of a CG iteration
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev_in = nullptr;
-  cudaGraphExec_t g1 = nullptr, g2 = nullptr;
-  long long g1_kernels = 0, g2_kernels = 0;
-};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
 
 namespace {
 
@@ -120,7 +40,7 @@ struct Carver {
   }
 };
 
-size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base) {
+size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, char* base, int mr_precision) {
   Carver c{base};
   const int np = H.np;
   const size_t nb2 = (size_t)np * np;
@@ -139,6 +59,7 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
   D.nbf = (int64_t)H.mesh.bf_K.size();
   D.precision = precision;
   const size_t vsz = precision ? sizeof(float) : sizeof(double);
+  D.nrhs = nrhs;
   for (int l = 0; l < nlev; ++l) {
     DevLevel& L = D.lev[l];
     const cdg::BSR& A = H.A_t[l];
@@ -213,6 +134,10 @@ size_t layout(const cdg::Hierarchy& H, int precision, DeviceState* S, char* base
   D.scal = c.take<double>((size_t)S_COUNT * D.nseg);
   D.npartial = std::max<int>(std::max(kDotBlocks, D.nseg * D.bps), (int)((int64_t)ne * np / 64 + 2));
   D.partial = c.take<double>((size_t)D.npartial * 2);
+  if (nrhs > 0) {
+    if (S && !S->mr) S->mr = mr_new();
+    c.off = mr_layout(H, nrhs, mr_precision, S ? S->mr : nullptr, base, c.off);
+  }
   return (c.off + 255) & ~size_t(255);
 }
 
@@ -973,7 +898,8 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
 }
 
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
-  *bytes = (int64_t)layout(h->H, h->opt.precision, nullptr, nullptr);
+  *bytes = (int64_t)layout(h->H, h->opt.precision == 2 ? 1 : h->opt.precision, h->opt.nrhs, nullptr, nullptr,
+                          h->opt.precision);
   return CDG_OK;
 }
 
@@ -987,6 +913,7 @@ void dev_release(cdg_handle* h) {
       cudaStreamDestroy(D.stream);
     }
     if (D.ev_in) cudaEventDestroy(D.ev_in);
+    mr_delete(D.mr);
   }
   delete h->dev;
   h->dev = nullptr;
@@ -994,7 +921,8 @@ void dev_release(cdg_handle* h) {
 
 int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   const cdg::Hierarchy& H = h->H;
-  const int64_t need = (int64_t)layout(H, h->opt.precision, nullptr, nullptr);
+  const int prec = h->opt.precision == 2 ? 1 : h->opt.precision;
+  const int64_t need = (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision);
   if (bytes < need) {
     h->err = "device buffer too small: need " + std::to_string(need) + " bytes";
     return CDG_ENOMEM;
@@ -1008,7 +936,8 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   DeviceState& D = *h->dev;
   D.base = (char*)buf;
   D.bytes = bytes;
-  layout(H, h->opt.precision, &D, (char*)buf);
+  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision);
+  D.precision = h->opt.precision == 2 ? 1 : h->opt.precision;
   cudaStream_t s = (cudaStream_t)stream;
   const int nlev = D.nlev;
   for (int l = 0; l < nlev; ++l) {
@@ -1069,6 +998,10 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   cudaError_t e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D.stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D.ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess && D.mr) {
+    mr_upload(H, *D.mr, s);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");

@@ -1,0 +1,620 @@
+// Many right-hand sides on one mesh (cdg_solve_multi): the same V-cycle
+// preconditioned CG run for R columns at once.  Vectors are [n_l][n_p][R]
+// (the R columns of one element's coefficient i are contiguous), so one block
+// of an operator is read once per R columns: a CTA owns one block row and its
+// R threads own one column each; the block is staged in shared memory and
+// every thread applies it to its column.  The outer CG (residual, dots, updates,
+// the level-0 operator) is FP64 with per-column scalars; the V-cycle runs on
+// FP32 (precision 1) or BF16 (precision 2) copies of the level operators with
+// FP32 arithmetic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "device_state.h"
+
+namespace {
+
+template <typename T>
+struct Conv;
+template <>
+struct Conv<double> {
+  static __device__ __forceinline__ double f(double v) { return v; }
+};
+template <>
+struct Conv<float> {
+  static __device__ __forceinline__ float f(float v) { return v; }
+};
+template <>
+struct Conv<__nv_bfloat16> {
+  static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+template <typename TA, typename TC>
+__device__ __forceinline__ void stage_block(TC* s, const TA* a, int ne) {
+  for (int t = threadIdx.x; t < ne; t += blockDim.x) s[t] = (TC)Conv<TA>::f(a[t]);
+}
+
+// y = A x (MODE 0), y = b - A x (1), y = x + omega (b - x - A x) (3; A = Ahat, b = D^-1 b)
+template <typename TA, typename TV, typename TC, int NP, int MODE>
+__global__ void mr_bsr_kernel(int R, const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const TA* __restrict__ A, const TV* __restrict__ x, const TV* __restrict__ b,
+                              TV* __restrict__ y, TC omega) {
+  __shared__ TC as[NP * NP];
+  const int K = blockIdx.x;
+  const int r = threadIdx.x;
+  TC acc[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) acc[i] = TC(0);
+  const int b0 = rowptr[K], b1 = rowptr[K + 1];
+  for (int bb = b0; bb < b1; ++bb) {
+    __syncthreads();
+    stage_block<TA, TC>(as, A + (size_t)bb * NP * NP, NP * NP);
+    __syncthreads();
+    if (r < R) {
+      const TV* xj = x + (size_t)col[bb] * NP * R + r;
+      TC xv[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) xv[j] = (TC)xj[(size_t)j * R];
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[i] = fma(as[i * NP + j], xv[j], acc[i]);
+    }
+  }
+  if (r >= R) return;
+  const size_t base = (size_t)K * NP * R + r;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const size_t o = base + (size_t)i * R;
+    if (MODE == 0) y[o] = (TV)acc[i];
+    else if (MODE == 1) y[o] = (TV)((TC)b[o] - acc[i]);
+    else y[o] = (TV)((TC)x[o] + omega * ((TC)b[o] - (TC)x[o] - acc[i]));
+  }
+}
+
+// per element K: out = B_K in (block-diagonal apply); with WRITE_X also x = omega out
+template <typename TA, typename TV, int NP, bool WRITE_X>
+__global__ void mr_diag_kernel(int R, const TA* __restrict__ B, const TV* __restrict__ in, TV* __restrict__ out,
+                               TV* __restrict__ x, float omega) {
+  __shared__ float as[NP * NP];
+  const int K = blockIdx.x;
+  const int r = threadIdx.x;
+  stage_block<TA, float>(as, B + (size_t)K * NP * NP, NP * NP);
+  __syncthreads();
+  if (r >= R) return;
+  const size_t base = (size_t)K * NP * R + r;
+  float v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) v[j] = (float)in[base + (size_t)j * R];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s = fmaf(as[i * NP + j], v[j], s);
+    out[base + (size_t)i * R] = (TV)s;
+    if (WRITE_X) x[base + (size_t)i * R] = (TV)(omega * s);
+  }
+}
+
+// bc[A] = sum over children K of L_K^T r[K]
+template <typename TA, typename TV, int NP>
+__global__ void mr_restrict_kernel(int R, const int* __restrict__ childptr, const TA* __restrict__ L,
+                                   const TV* __restrict__ rf, TV* __restrict__ bc) {
+  __shared__ float ls[NP * NP];
+  const int Ag = blockIdx.x;
+  const int r = threadIdx.x;
+  float acc[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) acc[i] = 0.f;
+  for (int K = childptr[Ag]; K < childptr[Ag + 1]; ++K) {
+    __syncthreads();
+    stage_block<TA, float>(ls, L + (size_t)K * NP * NP, NP * NP);
+    __syncthreads();
+    if (r < R) {
+      float v[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) v[j] = (float)rf[(size_t)K * NP * R + (size_t)j * R + r];
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[i] = fmaf(ls[j * NP + i], v[j], acc[i]);
+    }
+  }
+  if (r >= R) return;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) bc[(size_t)Ag * NP * R + (size_t)i * R + r] = (TV)acc[i];
+}
+
+// x[K] (+)= L_K xc[parent K]
+template <typename TA, typename TV, int NP, bool ADD>
+__global__ void mr_prolong_kernel(int R, const int* __restrict__ parent, const TA* __restrict__ L,
+                                  const TV* __restrict__ xc, TV* __restrict__ x) {
+  __shared__ float ls[NP * NP];
+  const int K = blockIdx.x;
+  const int r = threadIdx.x;
+  stage_block<TA, float>(ls, L + (size_t)K * NP * NP, NP * NP);
+  __syncthreads();
+  if (r >= R) return;
+  const TV* xa = xc + (size_t)parent[K] * NP * R + r;
+  float v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) v[j] = (float)xa[(size_t)j * R];
+  const size_t base = (size_t)K * NP * R + r;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s = fmaf(ls[i * NP + j], v[j], s);
+    x[base + (size_t)i * R] = ADD ? (TV)((float)x[base + (size_t)i * R] + s) : (TV)s;
+  }
+}
+
+// coarsest (one mesh): x[row][r] = sum_j Ainv[row][j] b[j][r], FP64 accumulation
+template <typename TV>
+__global__ void mr_coarse_kernel(int nc, int R, const double* __restrict__ Ainv, const TV* __restrict__ b,
+                                 TV* __restrict__ x) {
+  const int row = blockIdx.x;
+  const int r = threadIdx.x;
+  if (r >= R) return;
+  const double* a = Ainv + (size_t)row * nc;
+  double s = 0.0;
+  for (int j = 0; j < nc; ++j) s = fma(a[j], (double)b[(size_t)j * R + r], s);
+  x[(size_t)row * R + r] = (TV)s;
+}
+
+template <typename TI, typename TO>
+__global__ void mr_convert_kernel(size_t n, const TI* __restrict__ a, TO* __restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (TO)a[i];
+}
+
+// per-column partial dots over a chunk of rows: partial[g][r] (and [G + g][r] for w)
+__global__ void mr_dot_kernel(int nrows, int R, int G, const double* __restrict__ x, const double* __restrict__ y,
+                              const double* __restrict__ w, double* __restrict__ partial) {
+  const int g = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  const int lo = (int)((long long)nrows * g / G), hi = (int)((long long)nrows * (g + 1) / G);
+  double s = 0.0, s2 = 0.0;
+  for (int row = lo; row < hi; ++row) {
+    const size_t o = (size_t)row * R + r;
+    s = fma(x[o], y[o], s);
+    if (w) s2 = fma(x[o], w[o], s2);
+  }
+  partial[(size_t)g * R + r] = s;
+  if (w) partial[(size_t)(G + g) * R + r] = s2;
+}
+
+// per column: sum the G partials in order and update that column's CG scalars
+// (same rules as the single-column finalize: which 0 PQ, 1 RR, 2 RZ, 3 BB, 4 initial RR)
+__global__ void mr_finalize_kernel(int R, int G, const double* __restrict__ partial, int which, int flexible,
+                                   double tol, double* __restrict__ scal) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double tot = 0.0, tot2 = 0.0;
+  for (int g = 0; g < G; ++g) tot += partial[(size_t)g * R + r];
+  if (which == 2 && flexible)
+    for (int g = 0; g < G; ++g) tot2 += partial[(size_t)(G + g) * R + r];
+  double* sc = scal + (size_t)r * S_COUNT;
+  const bool done = sc[S_DONE] != 0.0;
+  if (which == 0) {
+    sc[S_PQ] = tot;
+    if (!done && !(tot > 0.0)) {
+      sc[S_BREAK] = 1.0;
+      sc[S_DONE] = 1.0;
+    }
+    sc[S_ALPHA] = sc[S_DONE] != 0.0 ? 0.0 : sc[S_RZ] / tot;
+  } else if (which == 1 || which == 4) {
+    if (!done) {
+      sc[S_RR] = tot;
+      if (which == 1) sc[S_IT] += 1.0;
+      if (!isfinite(tot)) {
+        sc[S_BREAK] = 1.0;
+        sc[S_DONE] = 1.0;
+      } else if (sqrt(tot) <= tol * sqrt(sc[S_BB])) {
+        sc[S_DONE] = 1.0;
+      }
+    }
+  } else if (which == 2) {
+    const double rz_old = sc[S_RZ];
+    sc[S_BETA] = done ? 0.0 : (flexible ? (tot - tot2) / rz_old : tot / rz_old);
+    sc[S_RZ] = tot;
+  } else {
+    sc[S_BB] = tot;
+    if (!(tot > 0.0)) sc[S_DONE] = 1.0;
+  }
+}
+
+// x += alpha_r p; r -= alpha_r q (per column) -- and p = z + beta_r p
+__global__ void mr_update_kernel(size_t nrows, int R, const double* __restrict__ scal, const double* __restrict__ p,
+                                 const double* __restrict__ q, double* __restrict__ x, double* __restrict__ res) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nrows * R; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % R);
+    const double a = scal[(size_t)r * S_COUNT + S_ALPHA];
+    x[t] = fma(a, p[t], x[t]);
+    res[t] = fma(-a, q[t], res[t]);
+  }
+}
+
+__global__ void mr_p_kernel(size_t nrows, int R, const double* __restrict__ scal, int first,
+                            const double* __restrict__ z, double* __restrict__ p) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nrows * R; t += (size_t)gridDim.x * blockDim.x) {
+    const double beta = first ? 0.0 : scal[(size_t)(t % R) * S_COUNT + S_BETA];
+    p[t] = first ? z[t] : fma(beta, p[t], z[t]);
+  }
+}
+
+// b[k][i][r] = sum_q w_q phi_i(x_q) f[r][K][q], K = perm0[k]  (f only; zero boundary data)
+template <int NP>
+__global__ void mr_rhs_kernel(int R, int nq, int ne, const int* __restrict__ perm0, const double* __restrict__ V,
+                              const double* __restrict__ f, double* __restrict__ b) {
+  const int k = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  const size_t K = perm0[k];
+  const double* fk = f + ((size_t)r * ne + K) * nq;
+  const double* Vk = V + (size_t)k * nq * NP;
+  double s[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) s[i] = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    const double fv = fk[q];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) s[i] = fma(Vk[q * NP + i], fv, s[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) b[((size_t)k * NP + i) * R + r] = s[i];
+}
+
+// u[r][K][i] = x[k][i][r] (user layout: one contiguous solution per column)
+__global__ void mr_out_kernel(int R, int np, const int* __restrict__ perm0, const double* __restrict__ x,
+                              int ne, double* __restrict__ u) {
+  const int k = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  const size_t K = perm0[k];
+  for (int i = 0; i < np; ++i) u[((size_t)r * ne + K) * np + i] = x[((size_t)k * np + i) * R + r];
+}
+
+}  // namespace
+
+struct MRLevel {
+  void* A = nullptr;      // V-cycle operator copies (FP32 or BF16)
+  void* Ahat = nullptr;
+  void* Dinv = nullptr;
+  void* L = nullptr;
+  float *x = nullptr, *t = nullptr, *r = nullptr, *b = nullptr, *bh = nullptr;
+};
+
+struct MR {
+  int R = 0, G = 0;
+  bool bf16 = false;
+  MRLevel lev[kMaxLev];
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr, *zold = nullptr;
+  float *r32 = nullptr, *z32 = nullptr;
+  double* scal = nullptr;      // [R][S_COUNT]
+  double* partial = nullptr;   // [2G][R]
+};
+
+namespace {
+
+struct MRCarver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+template <typename TA>
+void upload_conv(void* dst, const std::vector<double>& src, cudaStream_t s) {
+  if (src.empty()) return;
+  std::vector<TA> h(src.size());
+  for (size_t i = 0; i < src.size(); ++i) h[i] = (TA)src[i];
+  cudaMemcpyAsync(dst, h.data(), sizeof(TA) * h.size(), cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+MR* mr_new() { return new MR(); }
+void mr_delete(MR* m) { delete m; }
+
+// Carves the multi-column buffers after `off`; returns the new end offset.
+size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off) {
+  MRCarver c{base, off};
+  MR tmp;
+  MR& M = mr ? *mr : tmp;
+  M.R = R;
+  M.G = 2 * 152;
+  M.bf16 = precision == 2;
+  const size_t ts = M.bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
+  const int np = H.np;
+  const size_t nb2 = (size_t)np * np;
+  const int nlev = (int)H.lev.size();
+  for (int l = 0; l < nlev; ++l) {
+    MRLevel& L = M.lev[l];
+    const size_t n = (size_t)H.lev[l].n;
+    L.A = c.take<char>(H.A_t[l].val.size() * ts);
+    if (l + 1 < nlev) {
+      L.Ahat = c.take<char>(std::max<size_t>(1, H.Ahat_t[l].val.size()) * ts);
+      L.Dinv = c.take<char>(n * nb2 * ts);
+      L.L = c.take<char>(n * nb2 * ts);
+    }
+    L.x = c.take<float>(n * np * R);
+    L.t = c.take<float>(n * np * R);
+    L.r = c.take<float>(n * np * R);
+    L.b = c.take<float>(n * np * R);
+    L.bh = c.take<float>(n * np * R);
+  }
+  const size_t nv = (size_t)H.mesh.ne * np * R;
+  M.x = c.take<double>(nv);
+  M.r = c.take<double>(nv);
+  M.z = c.take<double>(nv);
+  M.p = c.take<double>(nv);
+  M.q = c.take<double>(nv);
+  M.bt = c.take<double>(nv);
+  M.zold = c.take<double>(nv);
+  M.r32 = c.take<float>(nv);
+  M.z32 = c.take<float>(nv);
+  M.scal = c.take<double>((size_t)R * S_COUNT);
+  M.partial = c.take<double>((size_t)2 * M.G * R);
+  return c.off;
+}
+
+void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s) {
+  const int nlev = (int)H.lev.size();
+  for (int l = 0; l < nlev; ++l) {
+    MRLevel& L = M.lev[l];
+    auto up = [&](void* dst, const std::vector<double>& src) {
+      if (!dst) return;
+      if (M.bf16) upload_conv<__nv_bfloat16>(dst, src, s);
+      else upload_conv<float>(dst, src, s);
+    };
+    up(L.A, H.A_t[l].val);
+    if (l + 1 < nlev) {
+      up(L.Ahat, H.Ahat_t[l].val);
+      up(L.Dinv, H.Dinv_t[l]);
+      up(L.L, H.L_t[l]);
+    }
+  }
+}
+
+namespace {
+
+#define MR_NP_DISPATCH(NPV, ...)                            \
+  switch (NPV) {                                            \
+    case 3: { constexpr int NP = 3; __VA_ARGS__; break; }   \
+    case 4: { constexpr int NP = 4; __VA_ARGS__; break; }   \
+    case 6: { constexpr int NP = 6; __VA_ARGS__; break; }   \
+    case 10: { constexpr int NP = 10; __VA_ARGS__; break; } \
+    default: return false;                                  \
+  }
+
+inline unsigned threads_for(int R) { return (unsigned)(((R + 31) / 32) * 32); }
+
+template <typename TA>
+bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, float* z0, cudaStream_t s) {
+  const int np = D.np, nlev = D.nlev, R = M.R;
+  const unsigned T = threads_for(R);
+  const float w = (float)o.omega;
+  auto bsr = [&](int mode, int l, const int* rp, const int* cl, const void* A, const float* x, const float* b,
+                 float* y) -> bool {
+    const int n = D.lev[l].n;
+    MR_NP_DISPATCH(np, {
+      if (mode == 1)
+        mr_bsr_kernel<TA, float, float, NP, 1><<<n, T, 0, s>>>(R, rp, cl, (const TA*)A, x, b, y, w);
+      else
+        mr_bsr_kernel<TA, float, float, NP, 3><<<n, T, 0, s>>>(R, rp, cl, (const TA*)A, x, b, y, w);
+    });
+    count_launch();
+    return true;
+  };
+  if (nlev == 1) {
+    mr_coarse_kernel<float><<<D.nc, T, 0, s>>>(D.nc, R, D.coarse_inv, b0, z0);
+    count_launch();
+    return true;
+  }
+  std::vector<const float*> bl(nlev);
+  bl[0] = b0;
+  for (int l = 1; l < nlev; ++l) bl[l] = M.lev[l].b;
+  for (int l = 0; l + 1 < nlev; ++l) {
+    MRLevel& L = M.lev[l];
+    const DevLevel& DL = D.lev[l];
+    float* x = L.x;
+    float* t = L.t;
+    const float* b = bl[l];
+    if (o.nu_pre >= 1) {
+      MR_NP_DISPATCH(np, mr_diag_kernel<TA, float, NP, true><<<DL.n, T, 0, s>>>(R, (const TA*)L.Dinv, b, L.bh, x, w));
+      count_launch();
+      for (int k = 1; k < o.nu_pre; ++k) {
+        if (!bsr(3, l, DL.hrowptr, DL.hcol, L.Ahat, x, L.bh, t)) return false;
+        std::swap(x, t);
+      }
+      if (!bsr(1, l, DL.rowptr, DL.col, L.A, x, b, L.r)) return false;
+      MR_NP_DISPATCH(np, mr_restrict_kernel<TA, float, NP><<<D.lev[l + 1].n, T, 0, s>>>(
+                             R, D.lev[l + 1].childptr, (const TA*)L.L, L.r, M.lev[l + 1].b));
+      count_launch();
+      L.x = x;
+      L.t = t;
+    } else {
+      MR_NP_DISPATCH(np, mr_diag_kernel<TA, float, NP, false><<<DL.n, T, 0, s>>>(R, (const TA*)L.Dinv, b, L.bh,
+                                                                                 (float*)nullptr, w));
+      MR_NP_DISPATCH(np, mr_restrict_kernel<TA, float, NP><<<D.lev[l + 1].n, T, 0, s>>>(
+                             R, D.lev[l + 1].childptr, (const TA*)L.L, b, M.lev[l + 1].b));
+      count_launch(2);
+    }
+  }
+  mr_coarse_kernel<float><<<D.nc, T, 0, s>>>(D.nc, R, D.coarse_inv, M.lev[nlev - 1].b, M.lev[nlev - 1].x);
+  count_launch();
+  for (int l = nlev - 2; l >= 0; --l) {
+    MRLevel& L = M.lev[l];
+    const DevLevel& DL = D.lev[l];
+    float* x = L.x;
+    float* t = L.t;
+    if (o.nu_pre >= 1) {
+      MR_NP_DISPATCH(np, mr_prolong_kernel<TA, float, NP, true><<<DL.n, T, 0, s>>>(R, DL.parent, (const TA*)L.L,
+                                                                                   M.lev[l + 1].x, x));
+    } else {
+      MR_NP_DISPATCH(np, mr_prolong_kernel<TA, float, NP, false><<<DL.n, T, 0, s>>>(R, DL.parent, (const TA*)L.L,
+                                                                                    M.lev[l + 1].x, x));
+    }
+    count_launch();
+    for (int k = 0; k < o.nu_post; ++k) {
+      float* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
+      if (!bsr(3, l, DL.hrowptr, DL.hcol, L.Ahat, x, L.bh, out)) return false;
+      if (out == t) std::swap(x, t);
+      else x = out;
+    }
+    if (l == 0 && o.nu_post == 0)
+      cudaMemcpyAsync(z0, x, sizeof(float) * (size_t)DL.n * np * R, cudaMemcpyDeviceToDevice, s);
+    if (l > 0 && x != L.x) {
+      L.t = L.x;
+      L.x = x;
+    }
+  }
+  return true;
+}
+
+bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t s) {
+  const DevLevel& L0 = D.lev[0];
+  const unsigned T = threads_for(M.R);
+  MR_NP_DISPATCH(D.np, mr_bsr_kernel<double, double, double, NP, 0><<<L0.n, T, 0, s>>>(
+                           M.R, L0.rowptr, L0.col, L0.A, x, (const double*)nullptr, y, 0.0));
+  count_launch();
+  return true;
+}
+
+void mr_dot(DeviceState& D, MR& M, const double* x, const double* y, const double* w, int which, double tol,
+            cudaStream_t s) {
+  const int nrows = (int)(D.ne * D.np);
+  const unsigned T = threads_for(M.R);
+  mr_dot_kernel<<<M.G, T, 0, s>>>(nrows, M.R, M.G, x, y, w, M.partial);
+  mr_finalize_kernel<<<(M.R + 127) / 128, 128, 0, s>>>(M.R, M.G, M.partial, which, w != nullptr, tol, M.scal);
+  count_launch(2);
+}
+
+}  // namespace
+
+// Solves A_0 U = B for R columns: f_q [R][n_elements][nq] (device), u [R][n_elements][n_p]
+// (device), res_hist [R][maxit+1] and iters [R] (host).
+int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int* iters, void* stream) {
+  if (!h->dev || !h->dev->mr) {
+    h->err = "cdg_solve_multi needs a handle created with nrhs > 0 and bound to a device buffer";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  MR& M = *D.mr;
+  const cdg_options& o = h->opt;
+  const int R = M.R;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaStream_t s = D.stream;
+  cudaEventRecord(D.ev_in, cs);
+  cudaStreamWaitEvent(s, D.ev_in, 0);
+  const size_t nv = (size_t)D.ne * D.np * R;
+  const size_t nrows = (size_t)D.ne * D.np;
+  const unsigned T = threads_for(R);
+  const unsigned gv = 4 * 152;
+  cudaMemsetAsync(M.scal, 0, sizeof(double) * (size_t)R * S_COUNT, s);
+  bool ok = true;
+  MR_NP_DISPATCH(D.np, mr_rhs_kernel<NP><<<(unsigned)D.ne, T, 0, s>>>(R, D.nq, (int)D.ne, D.perm0, D.rhs_vol, f_q, M.bt));
+  count_launch();
+  cudaMemsetAsync(M.x, 0, sizeof(double) * nv, s);
+  cudaMemcpyAsync(M.r, M.bt, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+  mr_dot(D, M, M.bt, M.bt, nullptr, 3, o.tol, s);
+  mr_dot(D, M, M.r, M.r, nullptr, 4, o.tol, s);
+  auto precond = [&]() -> bool {
+    mr_convert_kernel<double, float><<<gv, 256, 0, s>>>(nv, M.r, M.r32);
+    const bool r2 = M.bf16 ? mr_vcycle<__nv_bfloat16>(D, M, o, M.r32, M.z32, s)
+                           : mr_vcycle<float>(D, M, o, M.r32, M.z32, s);
+    mr_convert_kernel<float, double><<<gv, 256, 0, s>>>(nv, M.z32, M.z);
+    count_launch(2);
+    return r2;
+  };
+  std::vector<double> hs((size_t)R * S_COUNT);
+  cudaMemcpyAsync(hs.data(), M.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    h->err = std::string("solve_multi: ") + cudaGetErrorString(e);
+    return CDG_ECUDA;
+  }
+  const int stride = o.maxit + 1;
+  auto rel = [&](int r) {
+    const double* sc = &hs[(size_t)r * S_COUNT];
+    return sc[S_BB] > 0.0 ? std::sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
+  };
+  std::vector<char> done(R, 0);
+  int ndone = 0, status = CDG_OK, it = 0;
+  for (int r = 0; r < R; ++r) {
+    iters[r] = 0;
+    if (res_hist) res_hist[(size_t)r * stride] = rel(r);
+    if (hs[(size_t)r * S_COUNT + S_DONE] != 0.0) {
+      done[r] = 1;
+      ++ndone;
+    }
+  }
+  if (ndone < R) {
+    ok = precond();
+    mr_dot(D, M, M.r, M.z, nullptr, 2, o.tol, s);
+    mr_p_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, 1, M.z, M.p);
+    count_launch();
+    while (ok) {
+      if (it >= o.maxit) {
+        status = CDG_ENOCONV;
+        break;
+      }
+      ok = mr_apply64(D, M, M.p, M.q, s);
+      mr_dot(D, M, M.p, M.q, nullptr, 0, o.tol, s);
+      mr_update_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, M.p, M.q, M.x, M.r);
+      count_launch();
+      mr_dot(D, M, M.r, M.r, nullptr, 1, o.tol, s);
+      cudaMemcpyAsync(hs.data(), M.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        h->err = std::string("solve_multi: ") + cudaGetErrorString(e);
+        return CDG_ECUDA;
+      }
+      ++it;
+      for (int r = 0; r < R; ++r) {
+        if (done[r]) continue;
+        iters[r] = it;
+        if (res_hist) res_hist[(size_t)r * stride + it] = rel(r);
+        const double* sc = &hs[(size_t)r * S_COUNT];
+        if (sc[S_DONE] != 0.0) {
+          done[r] = 1;
+          ++ndone;
+          if (sc[S_BREAK] != 0.0) {
+            status = CDG_EBREAKDOWN;
+            h->err = "CG breakdown in column " + std::to_string(r);
+          }
+        }
+      }
+      if (ndone == R) break;
+      cudaMemcpyAsync(M.zold, M.z, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+      ok = precond();
+      mr_dot(D, M, M.r, M.z, M.zold, 2, o.tol, s);
+      mr_p_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, 0, M.z, M.p);
+      count_launch();
+    }
+  }
+  if (!ok) {
+    h->err = "unsupported n_p for cdg_solve_multi";
+    return CDG_EINVAL;
+  }
+  mr_out_kernel<<<(unsigned)D.ne, T, 0, s>>>(R, D.np, D.perm0, M.x, (int)D.ne, u);
+  count_launch();
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    h->err = std::string("solve_multi: ") + cudaGetErrorString(e);
+    return CDG_ECUDA;
+  }
+  if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
+  return status;
+}

@@ -1,0 +1,102 @@
+// Device-side state of a bound handle, shared by the solve-phase translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "handle.h"
+
+constexpr int kMaxLev = CDG_MAX_LEVELS;
+constexpr int kThreads = 256;
+constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
+
+// per-segment CG scalars (one row of S_COUNT doubles per mesh of the handle)
+enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, S_FLAG = 15, S_COUNT = 16 };
+
+struct DevLevel {
+  int n = 0;
+  int64_t nnzb = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* A = nullptr;
+  double* Dinv = nullptr;
+  double* L = nullptr;
+  int* parent = nullptr;
+  int* childptr = nullptr;   // children range of each element of this level (l >= 1)
+  float* A32 = nullptr;
+  float* Dinv32 = nullptr;
+  float* L32 = nullptr;
+  int* hrowptr = nullptr;    // Ahat = D^{-1}(A - D): row-scaled off-diagonal blocks (smoother)
+  int* hcol = nullptr;
+  double* Ahat = nullptr;
+  float* Ahat32 = nullptr;
+  int64_t hnnzb = 0;
+  void* bh = nullptr;        // D^{-1} b of the current V-cycle visit
+  void* x = nullptr;         // V-cycle work vectors in the V-cycle precision
+  void* t = nullptr;
+  void* r = nullptr;
+  void* b = nullptr;
+};
+
+struct DeviceState {
+  char* base = nullptr;
+  int64_t bytes = 0;
+  int nlev = 0, np = 0, d = 0, nq = 0, nfq = 0, precision = 0;
+  int64_t ne = 0, ndofs = 0, nbf = 0;
+  DevLevel lev[kMaxLev];
+  double* coarse_inv = nullptr;
+  int nc = 0;
+  double* coarse_b = nullptr;   // FP64 staging of the coarsest right-hand side / solution
+  double* coarse_x = nullptr;
+  // rhs data
+  double* rhs_vol = nullptr;
+  int* rhs_bptr = nullptr;
+  int* rhs_bface = nullptr;
+  double* rhs_bdata = nullptr;
+  int* btag = nullptr;
+  int* perm0 = nullptr;         // tree row -> user element
+  // d A_0 / d kappa pieces (tree order)
+  double* dk_own = nullptr;
+  int* dk_ptr = nullptr;
+  int* dk_nbr = nullptr;
+  double* dk_blk = nullptr;
+  double* kappa = nullptr;
+  // CG vectors (FP64, tree order)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr,
+         *zold = nullptr;
+  float *r32 = nullptr, *z32 = nullptr;
+  // staging for host-pointer solves
+  double *f_stage = nullptr, *gD_stage = nullptr, *gN_stage = nullptr, *u_stage = nullptr;
+  double* scal = nullptr;       // [nseg][S_COUNT]
+  double* partial = nullptr;
+  int npartial = 0;
+  // segments (meshes of a batched handle)
+  int nseg = 1, bps = 1;        // blocks per segment of the segmented vector kernels
+  long long* seg_dof = nullptr; // [nseg+1] level-0 dof offsets
+  int* crow_seg = nullptr;      // [nc] segment of each coarsest row
+  int* crow_off = nullptr;      // [nseg+1] coarsest row offsets
+  long long* cinv_off = nullptr;// [nseg+1] offsets of the dense inverses
+  std::vector<long long> h_seg_dof;
+  // private stream and the two captured graphs of a CG iteration
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr;
+  cudaGraphExec_t g1 = nullptr, g2 = nullptr;
+  long long g1_kernels = 0, g2_kernels = 0;
+  // multi-right-hand-side solve (cdg_solve_multi): R columns per vector
+  int nrhs = 0;
+  struct MR* mr = nullptr;   // device_multi.cu
+};
+
+// launch counter shared by all translation units
+void count_launch(long long n = 1);
+long long launch_count();
+
+
+// device_multi.cu
+namespace cdg { struct Hierarchy; }
+MR* mr_new();
+void mr_delete(MR* m);
+size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off);
+void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s);

@@ -31,3 +31,4 @@ long long dev_launch_count();
 int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b, double* y, void* stream);
 int dev_adjoint(cdg_handle* h, int what, const double* lam_user, const double* u_user, const double* gD,
                 double* out, void* stream);
+int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int* iters, void* stream);
