@@ -42,7 +42,10 @@ WORKLOADS = {
 }
 METRIC = "solved DOF/s (PCG+V-cycle to 1e-10)"
 HBM_FALLBACK_GBS = 6800.0           # profiling-recipe fallback when no measured peak file exists
-FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal)
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured 1.20
+# DRAM bytes (read + write) of one level-0 FP64 apply of the 512 x 512 p = 3 workload, from
+# the ncu capture summarised in profiles/ (None until captured for the current kernel)
+APPLY_TRAFFIC_BYTES = None
 
 
 def make_mesh(kind, n):
@@ -150,6 +153,105 @@ def cpu_baseline(kind, p, nu, seconds_target=10.0):
                       f"{its[0]} iterations, median of {len(times)} solves, set-up untimed"}
 
 
+def _time(fn, stream, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_extras(pkg, dev, stream, barrier):
+    """The other workloads of the solve phase, each timed after one warm-up:
+    64 meshes of 500-20000 triangles in one batched handle (p = 2) against the
+    same meshes solved one after another; one 158 x 158 x 2 triangle mesh
+    (p = 3) with 256 right-hand sides (sine combinations; FP32 and BF16 V-cycle blocks)
+    against 256 single solves estimated from 8; the differentiable 24^3 x 6
+    tetrahedra workload (p = 2, smoothed log-normal kappa): forward + adjoint."""
+    import torch
+    from synthetic import (batched_squares, face_neighbors, jittered_square, kuhn_cube, sin_source,
+                           sine_combination_sources, smoothed_lognormal_kappa)
+    out = {}
+    # ---- batched meshes
+    meshes = batched_squares(64, 500, 20000, seed=1)
+    B = pkg.BatchSolver(meshes, p=2, max_levels=4).bind(dev)
+    xq = B.quadrature_points()[0]
+    fq = torch.tensor(sin_source(xq), device=dev)
+    l0 = pkg.kernel_launches()
+    ms, (u, hists, its, rc) = _time(lambda: B.solve(fq), stream, 5)
+    nl = (pkg.kernel_launches() - l0) / 6
+    seq = 0.0
+    for m in meshes:
+        S = pkg.Solver(m, p=2, max_levels=4).bind(dev)
+        f1 = torch.tensor(sin_source(S.quadrature_points()[0]), device=dev)
+        t, _ = _time(lambda: S.solve(f1), stream, 1)
+        seq += t
+        del S
+    out["batched_64_meshes"] = {"value": B.info["n_dofs"] / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms,
+                                "dofs": B.info["n_dofs"], "iterations_min_max": [int(its.min()), int(its.max())],
+                                "rc": rc, "launches_per_solve": nl, "sequential_ms": seq,
+                                "speedup_vs_sequential": seq / ms}
+    del B
+    # ---- many right-hand sides on one mesh
+    mesh = jittered_square(158)
+    R = 256
+    S1 = pkg.Solver(mesh, p=3, max_levels=5, nu_pre=2, nu_post=2, precision="fp32").bind(dev)
+    xq = S1.quadrature_points()[0]
+    fq = torch.tensor(sine_combination_sources(xq, R, mmax=8, seed0=0), device=dev)
+    single = []
+    for r in range(8):
+        t, _ = _time(lambda: S1.solve(fq[r].contiguous()), stream, 1)
+        single.append(t)
+    del S1
+    for prec in ("fp32", "bf16"):
+        S = pkg.Solver(mesh, p=3, max_levels=5, nu_pre=2, nu_post=2, precision=prec, nrhs=R).bind(dev)
+        ms, (u, hists, its, rc) = _time(lambda: S.solve_multi(fq), stream, 2)
+        out["multi_rhs_256_" + prec] = {
+            "value": R * S.info["n_dofs"] / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms,
+            "dofs_per_rhs": S.info["n_dofs"], "nrhs": R, "vcycle_blocks": prec,
+            "iterations_min_max": [int(its.min()), int(its.max())], "rc": rc,
+            "single_rhs_fp32_vcycle_ms": float(np.mean(single)),
+            "speedup_vs_single_solves": R * float(np.mean(single)) / ms}
+        del S
+    # ---- differentiable solve
+    from paper_2012_08024_gb300.autograd import CDGSolve, SolverCache
+    mesh = kuhn_cube(24)
+    nb = face_neighbors(mesh)
+    kappa = smoothed_lognormal_kappa(nb, seed=2)
+    kstar = smoothed_lognormal_kappa(nb, seed=3)
+    # primal coarsening: with this kappa contrast (~1e3) the flux-coarsened 3D operators are indefinite
+    cache = SolverCache(mesh, p=2, max_levels=5, coarsen="primal")
+    xq = cache.get(torch.tensor(kstar), dev).quadrature_points()[0]
+    fq = torch.tensor(sin_source(xq), device=dev)
+    with torch.no_grad():
+        ut = CDGSolve.apply(fq, torch.tensor(kstar, device=dev), cache)
+    k = torch.tensor(kappa, device=dev, requires_grad=True)
+    f = fq.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    loss = ((CDGSolve.apply(f, k, cache) - ut) ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    S = cache.solver
+    fw, _ = _time(lambda: S.solve(fq), stream, 2)
+    u = S.solve(fq)[0]
+    lam = S.solve_adjoint(2 * (u - ut))[0]
+    bw, _ = _time(lambda: (S.solve_adjoint(2 * (u - ut)), S.rhs_adjoint(lam), S.kappa_gradient(lam, u)), stream, 2)
+    kg, _ = _time(lambda: S.kappa_gradient(lam, u), stream, 10)
+    out["adjoint_24cube"] = {"elements": mesh.n_elements, "dofs": S.info["n_dofs"],
+                             "forward_ms": fw, "backward_ms": bw, "kappa_gradient_kernel_ms": kg,
+                             "first_forward_with_setup_s": t1 - t0, "first_backward_s": t2 - t1,
+                             "loss": float(loss)}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -193,6 +295,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tri512_p3", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batched / multi-RHS / adjoint workloads")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="override the workload's V-cycle precision")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -209,6 +315,8 @@ def main():
     import paper_2012_08024_gb300 as pkg
     from synthetic import sin_source
     kind, n, p, lv, nu, prec = WORKLOADS[args.workload]
+    if args.precision:
+        prec = args.precision
     mesh = make_mesh(kind, n)
     t0 = time.perf_counter()
     S = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10, maxit=500)
@@ -307,6 +415,12 @@ def main():
                  "rel_l2_diff_vs_fp64_solve": float((u32 - u64).norm() / u64.norm()),
                  "speedup_vs_fp64": ms / ms32}
         del S32
+    extras = {}
+    if args.extras and prec == "fp64":
+        try:
+            extras = run_extras(pkg, dev, stream, barrier)
+        except Exception as e:   # the headline line is printed regardless
+            extras = {"extras_error": repr(e)[:300]}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -324,14 +438,17 @@ def main():
                    "smoother": f"V({nu},{nu}) block Jacobi omega=2/3", "tol": 1e-10, "precision": prec,
                    "iterations": iters[-1], "setup_s": round(setup_s, 3), "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (operator %.2f GB)" % (S.info["device_bytes"] / 1e9)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+        "roofline": {"bound": "alu", "achieved": flops / (k_us * 1e-6) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flops / (k_us * 1e-6) / 1e12 / FP64_NOMINAL_TFLOPS,
+                     "traffic": APPLY_TRAFFIC_BYTES, "peak_source": "nominal FP64 (recipe table)",
                      "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0>)" % npb,
-                     "alg_bytes_per_launch": alg_bytes, "launch_us": k_us,
-                     "fp64_tflops": flops / (k_us * 1e-6) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS},
+                     "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
+                     "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
+                     "hbm_frac": achieved / peak},
         "e2e": {"value": ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
         "mixed_fp32_vcycle": mixed,
+        **extras,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

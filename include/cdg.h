@@ -75,7 +75,9 @@ typedef struct {
   int32_t max_levels;       /* levels including level 0 (Algorithm 1 stops earlier at 1 element) */
   uint64_t seed;            /* tie-break seed of Algorithm 2 */
   int32_t precision;        /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 CG;
-                               2: BF16 V-cycle blocks (FP32 arithmetic) for cdg_solve_multi */
+                               2: for cdg_solve_multi, BF16 row-scaled smoother blocks and
+                                  transfer blocks (FP32 residual operator, block inverses
+                                  and arithmetic) */
   int32_t switch_kind;      /* 0: directional consistent switch, 1: natural switch (Section 2.2) */
   const int8_t* face_switch;   /* nullable: S_{K1}^{K2} per interior face (library face order) */
   const int64_t* enumeration;  /* nullable: element enumeration N(K) of the natural switch */
@@ -175,8 +177,9 @@ int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double
  * scalars.  f_q [R][n_elements][nq] device (zero boundary data), u
  * [R][n_elements][n_p] device, res_hist [R][maxit+1] and iters [R] host.
  * Vectors are stored [element][n_p][R] on the device so every operator block
- * is read once per R columns; the V-cycle uses FP32 (precision 1) or BF16
- * (precision 2) block copies with FP32 arithmetic, the outer CG is FP64. */
+ * is read once per R columns; the V-cycle computes in FP32 on FP32 block copies
+ * (precision 1) or on BF16 row-scaled smoother and transfer blocks with FP32
+ * residual operator and block inverses (precision 2); the outer CG is FP64. */
 int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int32_t* iters, void* stream);
 
 /* Same solve from a given load vector b (device, user order, [n_elements][n_p]). */

@@ -5,8 +5,9 @@
 // R threads own one column each; the block is staged in shared memory and
 // every thread applies it to its column.  The outer CG (residual, dots, updates,
 // the level-0 operator) is FP64 with per-column scalars; the V-cycle runs on
-// FP32 (precision 1) or BF16 (precision 2) copies of the level operators with
-// FP32 arithmetic.
+// FP32 arithmetic on FP32 copies of the level operators, or (precision 2) on
+// BF16 copies of the row-scaled smoother blocks D^-1(A - D) and of the transfer
+// blocks (the residual operator and the block inverses stay FP32).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -341,10 +342,14 @@ size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* ba
   for (int l = 0; l < nlev; ++l) {
     MRLevel& L = M.lev[l];
     const size_t n = (size_t)H.lev[l].n;
-    L.A = c.take<char>(H.A_t[l].val.size() * ts);
+    // the residual operator stays FP32 in every mode: b - A x cancels, and BF16
+    // blocks (8-bit significands) would leave only noise in a small residual
+    L.A = c.take<char>(H.A_t[l].val.size() * sizeof(float));
     if (l + 1 < nlev) {
       L.Ahat = c.take<char>(std::max<size_t>(1, H.Ahat_t[l].val.size()) * ts);
-      L.Dinv = c.take<char>(n * nb2 * ts);
+      // block inverses stay FP32 too: with C_D = gamma/h_avg a diagonal block reaches
+      // cond ~1e5, and an 8-bit rounding of its inverse is then no inverse at all
+      L.Dinv = c.take<char>(n * nb2 * sizeof(float));
       L.L = c.take<char>(n * nb2 * ts);
     }
     L.x = c.take<float>(n * np * R);
@@ -377,10 +382,10 @@ void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s) {
       if (M.bf16) upload_conv<__nv_bfloat16>(dst, src, s);
       else upload_conv<float>(dst, src, s);
     };
-    up(L.A, H.A_t[l].val);
+    upload_conv<float>(L.A, H.A_t[l].val, s);
     if (l + 1 < nlev) {
       up(L.Ahat, H.Ahat_t[l].val);
-      up(L.Dinv, H.Dinv_t[l]);
+      upload_conv<float>(L.Dinv, H.Dinv_t[l], s);
       up(L.L, H.L_t[l]);
     }
   }
@@ -409,7 +414,7 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
     const int n = D.lev[l].n;
     MR_NP_DISPATCH(np, {
       if (mode == 1)
-        mr_bsr_kernel<TA, float, float, NP, 1><<<n, T, 0, s>>>(R, rp, cl, (const TA*)A, x, b, y, w);
+        mr_bsr_kernel<float, float, float, NP, 1><<<n, T, 0, s>>>(R, rp, cl, (const float*)A, x, b, y, w);
       else
         mr_bsr_kernel<TA, float, float, NP, 3><<<n, T, 0, s>>>(R, rp, cl, (const TA*)A, x, b, y, w);
     });
@@ -431,7 +436,7 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
     float* t = L.t;
     const float* b = bl[l];
     if (o.nu_pre >= 1) {
-      MR_NP_DISPATCH(np, mr_diag_kernel<TA, float, NP, true><<<DL.n, T, 0, s>>>(R, (const TA*)L.Dinv, b, L.bh, x, w));
+      MR_NP_DISPATCH(np, mr_diag_kernel<float, float, NP, true><<<DL.n, T, 0, s>>>(R, (const float*)L.Dinv, b, L.bh, x, w));
       count_launch();
       for (int k = 1; k < o.nu_pre; ++k) {
         if (!bsr(3, l, DL.hrowptr, DL.hcol, L.Ahat, x, L.bh, t)) return false;
@@ -444,8 +449,8 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
       L.x = x;
       L.t = t;
     } else {
-      MR_NP_DISPATCH(np, mr_diag_kernel<TA, float, NP, false><<<DL.n, T, 0, s>>>(R, (const TA*)L.Dinv, b, L.bh,
-                                                                                 (float*)nullptr, w));
+      MR_NP_DISPATCH(np, mr_diag_kernel<float, float, NP, false><<<DL.n, T, 0, s>>>(R, (const float*)L.Dinv, b,
+                                                                                    L.bh, (float*)nullptr, w));
       MR_NP_DISPATCH(np, mr_restrict_kernel<TA, float, NP><<<D.lev[l + 1].n, T, 0, s>>>(
                              R, D.lev[l + 1].childptr, (const TA*)L.L, b, M.lev[l + 1].b));
       count_launch(2);

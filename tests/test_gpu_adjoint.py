@@ -82,7 +82,7 @@ def test_finite_differences_20_directions():
     import torch
     from paper_2012_08024_gb300.autograd import CDGSolve, SolverCache
     mesh, kappa, kstar = _workload(6)
-    opts = dict(p=2, max_levels=4, tol=1e-12, maxit=2000)
+    opts = dict(p=2, max_levels=4, tol=1e-12, maxit=2000, coarsen="primal")
     cache = SolverCache(mesh, **opts)
     xq = cache.get(torch.tensor(kstar), "cuda").quadrature_points()[0]
     fq = _t(sin_source(xq))
