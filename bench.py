@@ -333,14 +333,17 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- device-resident solves
-    for _ in range(max(args.warmup, 3)):
-        u, hist, it, rc = S.solve(fq)
-    barrier()
-    l0 = pkg.kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters = []
-    with ClockSampler(dev.index) as cs:
+    # ---- device-resident solves (the clock sampler starts before the warm-up: nvidia-smi's
+    # own start-up must not fall inside a short timed region)
+    cs = ClockSampler(dev.index)
+    with cs:
+        time.sleep(1.0)
+        for _ in range(max(args.warmup, 3)):
+            u, hist, it, rc = S.solve(fq)
+        barrier()
+        l0 = pkg.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = []
         e0.record(stream)
         for _ in range(args.steps):
             u, hist, it, rc = S.solve(fq)
