@@ -207,12 +207,25 @@ __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restr
       const T* xj = x + (size_t)J * NP;
       if constexpr (VEC) {
         // even n_p: the row of the block and x_J are 8-byte (FP32) / 16-byte
-        // (FP64) aligned runs, read as float2 / double2
+        // (FP64) aligned runs, read as float2 / double2; two blocks per step
+        // keep twice the loads in flight
         T av[NP], xv[NP];
         VecLoad<T, NP>::load(a, av);
         VecLoad<T, NP>::load(xj, xv);
+        if (bb + 1 < b1) {
+          const int J2 = ldg(col + bb + 1);
+          T av2[NP], xv2[NP];
+          VecLoad<T, NP>::load(a + NP * NP, av2);
+          VecLoad<T, NP>::load(x + (size_t)J2 * NP, xv2);
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+          for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+#pragma unroll
+          for (int j = 0; j < NP; ++j) acc = fma(av2[j], xv2[j], acc);
+          ++bb;
+        } else {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
