@@ -46,7 +46,7 @@ extern "C" {
 #define CDG_EINVAL 1      /* null pointer, bad size or option */
 #define CDG_EMESH 2       /* degenerate element, non-manifold face, no Dirichlet boundary */
 #define CDG_ENOCONV 3     /* maxit reached; outputs are still written */
-#define CDG_EBREAKDOWN 4  /* p^T A p <= 0 or a non-finite residual in CG */
+#define CDG_EBREAKDOWN 4  /* p^T A p <= 0 in CG, a singular GMRES Hessenberg, or a non-finite residual */
 #define CDG_ECUDA 5       /* a CUDA runtime call failed */
 #define CDG_ETIMEOUT 6    /* a bounded device wait expired */
 #define CDG_ENOMEM 7      /* host allocation failed or device buffer too small */
@@ -86,6 +86,11 @@ typedef struct {
   double tol;               /* relative residual ||r||/||b|| to stop CG, default 1e-10 */
   int32_t maxit;            /* CG iteration limit, default 500 */
   int32_t nrhs;             /* columns of cdg_solve_multi (0 = none), at most 1024 */
+  int32_t krylov;           /* outer Krylov method of cdg_solve: 0 CG (A_0 is SPD; needs a
+                               symmetric V-cycle, nu_pre = nu_post), 1 restarted GMRES with
+                               the V-cycle as right preconditioner (Section 4; flexible form,
+                               single-mesh handles only) */
+  int32_t restart;          /* GMRES restart length m in [1, 512], default 50 (Section 5) */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16
@@ -104,7 +109,8 @@ typedef struct {
 } cdg_info;
 
 /* Defaults: p=2, gamma=1e4, V(1,1), omega=2/3, 4 levels, seed 0, FP64,
- * directional switch, flux coarsening, tol=1e-10, maxit=500. */
+ * directional switch, flux coarsening, tol=1e-10, maxit=500, CG (restart 50
+ * when GMRES is selected). */
 void cdg_default_options(cdg_options* opt);
 
 /* Host set-up (Sections 2-4.1): faces, switch, quadrature, bases, level-0 CDG
@@ -167,8 +173,14 @@ int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD_q, const double* 
  * res_hist are host arrays (copied in and out inside the call); else device
  * arrays (res_hist may then be a host array too: it is always written from
  * the host).  The solve runs on a private stream of the handle, ordered after
- * the work already queued on `stream`; it returns when the solution is written.  Errors: CDG_ESTATE, CDG_ENOCONV,
- * CDG_EBREAKDOWN, CDG_ECUDA. */
+ * the work already queued on `stream`; it returns when the solution is written.
+ * With krylov = 1 the outer method is restarted GMRES(restart) with the V-cycle
+ * as right preconditioner (Section 4), in the flexible form that stores the
+ * preconditioned vectors; iterations count Arnoldi steps, res_hist[k] is the
+ * least-squares residual estimate |g_{k+1}|/||b|| (the true residual after a
+ * restart or at the end), and a happy breakdown ends the solve as converged.
+ * Errors: CDG_ESTATE, CDG_ENOCONV, CDG_EBREAKDOWN (CG: p^T A p <= 0; GMRES: a
+ * singular Hessenberg column; both: a non-finite residual), CDG_ECUDA. */
 int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double* gN_q, double* u,
               int32_t use_u0, double* res_hist, int32_t* iters, int32_t host_pointers, void* stream);
 

@@ -38,7 +38,8 @@ class cdg_options(C.Structure):
                 ("omega", C.c_double), ("max_levels", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
-                ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32)]
+                ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
+                ("krylov", C.c_int32), ("restart", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -124,6 +125,7 @@ def _stream_ptr(stream) -> int | None:
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 COARSEN = {"flux": 0, "primal": 1}
+KRYLOV = {"cg": 0, "gmres": 1}
 
 
 class Solver:
@@ -132,7 +134,8 @@ class Solver:
     def __init__(self, mesh, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
-                 coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0):
+                 coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
+                 krylov: str = "cg", restart: int = 50):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -150,6 +153,7 @@ class Solver:
         o.precision, o.switch_kind = PRECISION[precision], switch_kind
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
         o.nrhs = nrhs
+        o.krylov, o.restart = KRYLOV[krylov], restart
         arrs = {}
         if face_switch is not None:
             arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)

@@ -35,6 +35,9 @@ static int check_options(const cdg_options* opt) {
   if (opt->nrhs < 0 || opt->nrhs > 1024) return fail(nullptr, CDG_EINVAL, "nrhs must be in [0, 1024]");
   if (opt->precision == 2 && opt->nrhs == 0)
     return fail(nullptr, CDG_EINVAL, "precision 2 (BF16 blocks) is the multi-right-hand-side mode: set nrhs");
+  if (opt->krylov < 0 || opt->krylov > 1) return fail(nullptr, CDG_EINVAL, "krylov must be 0 (CG) or 1 (GMRES)");
+  if (opt->krylov == 1 && (opt->restart < 1 || opt->restart > 512))
+    return fail(nullptr, CDG_EINVAL, "GMRES restart must be in [1, 512]");
   return CDG_OK;
 }
 
@@ -163,6 +166,8 @@ void cdg_default_options(cdg_options* o) {
   o->coarsen = 0;
   o->tol = 1e-10;
   o->maxit = 500;
+  o->krylov = 0;
+  o->restart = 50;
 }
 
 const char* cdg_last_error(const cdg_handle* h) {
@@ -193,6 +198,7 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
   if (!meshes || !opt || n_meshes < 1) return fail(nullptr, CDG_EINVAL, "meshes, n_meshes or options invalid");
   if (opt->kappa || opt->face_switch || opt->enumeration || opt->nrhs)
     return fail(nullptr, CDG_EINVAL, "per-element arrays and nrhs are not supported for batched handles");
+  if (opt->krylov != 0) return fail(nullptr, CDG_EINVAL, "batched handles solve with CG (krylov = 0)");
   int rc = check_options(opt);
   for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
   if (rc != CDG_OK) return rc;

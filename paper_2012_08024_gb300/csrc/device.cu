@@ -40,7 +40,8 @@ struct Carver {
   }
 };
 
-size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, char* base, int mr_precision) {
+size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, char* base, int mr_precision,
+              int gmres_m) {
   Carver c{base};
   const int np = H.np;
   const size_t nb2 = (size_t)np * np;
@@ -134,6 +135,14 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   D.scal = c.take<double>((size_t)S_COUNT * D.nseg);
   D.npartial = std::max<int>(std::max(kDotBlocks, D.nseg * D.bps), (int)((int64_t)ne * np / 64 + 2));
   D.partial = c.take<double>((size_t)D.npartial * 2);
+  if (gmres_m > 0) {
+    D.gm_m = gmres_m;
+    D.gm_ld = (vecbytes_elems + 31) & ~size_t(31);   // every basis vector starts 256-byte aligned
+    D.gm_V = c.take<double>((size_t)(gmres_m + 1) * D.gm_ld);
+    D.gm_Z = c.take<double>((size_t)gmres_m * D.gm_ld);
+    D.gm_part = c.take<double>((size_t)(gmres_m + 2) * kGmBlocks);
+    D.gm_st = c.take<double>((size_t)GmLayout{gmres_m}.size());
+  }
   if (nrhs > 0) {
     if (S && !S->mr) S->mr = mr_new();
     c.off = mr_layout(H, nrhs, mr_precision, S ? S->mr : nullptr, base, c.off);
@@ -849,6 +858,26 @@ std::vector<int> to_i32(const std::vector<int64_t>& v) {
 // ------------------------------------------------------------------ entry points
 long long dev_launch_count() { return g_launches.load(); }
 
+int dev_precond(cdg_handle* h, const double* r, double* z, cudaStream_t s) { return precond(h, r, z, s); }
+
+int dev_apply0(cdg_handle* h, int mode, const double* x, const double* b, double* y, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  const DevLevel& L0 = D.lev[0];
+  if (!launch_bsr<double>(mode, D.np, L0.n, L0.rowptr, L0.col, L0.A, x, b, y, h->opt.omega, nullptr, s,
+                          D.scal + S_FLAG)) {
+    h->err = "unsupported number of basis functions per element";
+    return CDG_EINVAL;
+  }
+  CDG_CHECK_LAUNCH(h, "level-0 operator");
+  return CDG_OK;
+}
+
+int dev_dot(cdg_handle* h, const double* x, const double* y, int which, cudaStream_t s) {
+  return dot_to(h, x, y, nullptr, which, s);
+}
+
+int dev_cuda_fail(cdg_handle* h, cudaError_t e, const char* where) { return cuda_fail(h, e, where); }
+
 // ------------------------------------------------------------------ allocation-free smoother
 // Fixed scratch for cdg_smooth_static: holds D^{-1} b of one level.  Every call
 // in the process shares it; nothing has to start at zero (the first kernel
@@ -910,9 +939,11 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
   return CDG_OK;
 }
 
+static int gmres_len(const cdg_options& o) { return o.krylov == 1 ? o.restart : 0; }
+
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
   *bytes = (int64_t)layout(h->H, h->opt.precision == 2 ? 1 : h->opt.precision, h->opt.nrhs, nullptr, nullptr,
-                          h->opt.precision);
+                          h->opt.precision, gmres_len(h->opt));
   return CDG_OK;
 }
 
@@ -921,6 +952,7 @@ void dev_release(cdg_handle* h) {
     DeviceState& D = *h->dev;
     if (D.g1) cudaGraphExecDestroy(D.g1);
     if (D.g2) cudaGraphExecDestroy(D.g2);
+    gmres_release(D);
     if (D.stream) {
       cudaStreamSynchronize(D.stream);
       cudaStreamDestroy(D.stream);
@@ -935,7 +967,7 @@ void dev_release(cdg_handle* h) {
 int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   const cdg::Hierarchy& H = h->H;
   const int prec = h->opt.precision == 2 ? 1 : h->opt.precision;
-  const int64_t need = (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision);
+  const int64_t need = (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision, gmres_len(h->opt));
   if (bytes < need) {
     h->err = "device buffer too small: need " + std::to_string(need) + " bytes";
     return CDG_ENOMEM;
@@ -949,7 +981,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   DeviceState& D = *h->dev;
   D.base = (char*)buf;
   D.bytes = bytes;
-  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision);
+  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision, gmres_len(h->opt));
   D.precision = h->opt.precision == 2 ? 1 : h->opt.precision;
   cudaStream_t s = (cudaStream_t)stream;
   const int nlev = D.nlev;
@@ -1232,7 +1264,14 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   }
   int status = CDG_OK;
   int it = 0;
-  if (ndone < nseg) {
+  if (o.krylov == 1) {
+    if (ndone < nseg) {
+      status = gmres_run(h, s, res_hist, iters);
+      if (status != CDG_OK && status != CDG_ENOCONV && status != CDG_EBREAKDOWN) return status;
+      it = iters[0];
+      done[0] = status != CDG_ENOCONV;
+    }
+  } else if (ndone < nseg) {
     if ((rc = precond(h, D.r, D.z, s)) != CDG_OK) return rc;
     if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
     launch(cg_p_kernel, (unsigned)(nseg * D.bps), kThreads, s, (const long long*)D.seg_dof, D.bps,

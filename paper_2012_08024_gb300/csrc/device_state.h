@@ -87,11 +87,52 @@ struct DeviceState {
   // multi-right-hand-side solve (cdg_solve_multi): R columns per vector
   int nrhs = 0;
   struct MR* mr = nullptr;   // device_multi.cu
+  // restarted flexible GMRES (device_gmres.cu): Krylov basis V, preconditioned
+  // vectors Z (row stride gm_ld), dot partials and the small Arnoldi state
+  int gm_m = 0;
+  size_t gm_ld = 0;
+  double* gm_V = nullptr;    // [m+1][gm_ld]
+  double* gm_Z = nullptr;    // [m][gm_ld]
+  double* gm_part = nullptr; // [m+2][kGmBlocks]
+  double* gm_st = nullptr;   // GmLayout(m).size() doubles
+  cudaGraphExec_t gm_step = nullptr;
+  long long gm_step_kernels = 0;
 };
+
+// blocks of the GMRES vector kernels (fixed: the dot partials are summed in a fixed order)
+constexpr int kGmBlocks = 4 * 152;
+
+// Offsets of the Arnoldi state of GMRES(m) in DeviceState::gm_st.
+struct GmLayout {
+  int m;
+  __host__ __device__ int h() const { return 0; }                // [m+1] projection coefficients of step j
+  __host__ __device__ int h2() const { return m + 1; }           // [m+1] second (re-orthogonalisation) pass
+  __host__ __device__ int R() const { return 2 * (m + 1); }      // [m][m] rotated Hessenberg, column-major
+  __host__ __device__ int cs() const { return R() + m * m; }     // [m] plane rotations
+  __host__ __device__ int sn() const { return cs() + m; }
+  __host__ __device__ int g() const { return sn() + m; }         // [m+1] rotated ||r0|| e1
+  __host__ __device__ int y() const { return g() + m + 1; }      // [m] least-squares solution
+  __host__ __device__ int misc() const { return y() + m; }       // see GmMisc
+  __host__ __device__ int size() const { return misc() + 8; }
+};
+enum GmMisc { GM_WN0 = 0, GM_WN1, GM_HNEXT, GM_REORTH, GM_J };
 
 // launch counter shared by all translation units
 void count_launch(long long n = 1);
 long long launch_count();
+
+// device.cu, for the GMRES driver: one V-cycle z = M^{-1} r on level-0 vectors;
+// y = A_0 x (mode 0) or y = b - A_0 x (mode 1) on 256-byte aligned tree-order
+// vectors; a level-0 dot into the CG scalars (dot_to's `which`); CUDA error text
+int dev_precond(cdg_handle* h, const double* r, double* z, cudaStream_t s);
+int dev_apply0(cdg_handle* h, int mode, const double* x, const double* b, double* y, cudaStream_t s);
+int dev_dot(cdg_handle* h, const double* x, const double* y, int which, cudaStream_t s);
+int dev_cuda_fail(cdg_handle* h, cudaError_t e, const char* where);
+
+// device_gmres.cu: the GMRES iteration of cdg_solve from x, r = b - A x and the
+// scalars S_BB, S_RR, S_DONE already on the device (single segment)
+int gmres_run(cdg_handle* h, cudaStream_t s, double* res_hist, int* iters);
+void gmres_release(DeviceState& D);
 
 
 // device_multi.cu

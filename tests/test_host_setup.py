@@ -105,3 +105,20 @@ def test_errors_are_reported():
     with pytest.raises(CdgError) as e:
         Solver(m, p=0)
     assert e.value.code == 1
+
+
+def test_gmres_options_and_device_bytes():
+    """GMRES(m) (Section 4) is an option of cdg_solve: checked at creation, and
+    its Krylov storage (m + 1 basis and m preconditioned vectors) is part of
+    the device buffer."""
+    from paper_2012_08024_gb300 import CdgError, Solver
+    m = jittered_square(6)
+    cg = Solver(m, p=2)
+    gm = Solver(m, p=2, nu_pre=0, nu_post=3, krylov="gmres", restart=10)
+    ndofs = cg.info["n_dofs"]
+    extra = gm.info["device_bytes"] - cg.info["device_bytes"]
+    assert 21 * ndofs * 8 <= extra <= 21 * (ndofs + 32) * 8 + 64 * 1024
+    for kw in (dict(krylov="gmres", restart=0), dict(krylov="gmres", restart=513)):
+        with pytest.raises(CdgError) as e:
+            Solver(m, p=1, **kw)
+        assert e.value.code == 1 and "restart" in str(e.value)
