@@ -43,9 +43,11 @@ WORKLOADS = {
 METRIC = "solved DOF/s (PCG+V-cycle to 1e-10)"
 HBM_FALLBACK_GBS = 6800.0           # profiling-recipe fallback when no measured peak file exists
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured 1.20
-# DRAM bytes (read + write) of one level-0 FP64 apply of the 512 x 512 p = 3 workload, from
-# the ncu capture summarised in profiles/ (None until captured for the current kernel)
-APPLY_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one level-0 FP64 apply of the 512 x 512 p = 3 workload: the ncu
+# capture of the same kernel on the 256 x 256 workload (443,725,568 bytes, profiles/
+# bsr_kernel_tri256_p3_fp64.md) scaled by the block count, exactly 4x (set to None whenever
+# bsr_kernel changes, until it is captured again)
+APPLY_TRAFFIC_BYTES = 4 * 443_725_568
 
 
 def make_mesh(kind, n):
@@ -418,6 +420,31 @@ def main():
                  "rel_l2_diff_vs_fp64_solve": float((u32 - u64).norm() / u64.norm()),
                  "speedup_vs_fp64": ms / ms32}
         del S32
+    # ---- the paper's own solver settings on the same mesh (Section 5): GMRES(50) right-
+    # preconditioned by V(0,3), tol 1e-8, hierarchy to one element
+    paper_solver = None
+    if args.extras and prec == "fp64":
+        paper_solver = {}
+        try:
+            for pr in ("fp64", "fp32"):
+                Sg = pkg.Solver(mesh, p=p, max_levels=16, nu_pre=0, nu_post=3, precision=pr, tol=1e-8,
+                                maxit=500, krylov="gmres", restart=50).bind(dev)
+                for _ in range(2):
+                    ug, hg, itg, rcg = Sg.solve(fq)
+                barrier()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    ug, hg, itg, rcg = Sg.solve(fq)
+                e1.record(stream)
+                barrier()
+                msg = e0.elapsed_time(e1) / args.steps
+                paper_solver["vcycle_" + pr] = {
+                    "value": ndof * ws / (msg * 1e-3), "unit": "DOF/s", "ms_per_step": msg, "iterations": itg,
+                    "levels": Sg.n_levels, "rc": rcg, "final_rel_residual": float(hg[-1]),
+                    "ms_per_arnoldi_step": msg / max(itg, 1)}
+                del Sg
+        except Exception as e:
+            paper_solver["error"] = repr(e)[:300]
     extras = {}
     if args.extras and prec == "fp64":
         try:
@@ -444,13 +471,14 @@ def main():
         "roofline": {"bound": "alu", "achieved": flops / (k_us * 1e-6) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": flops / (k_us * 1e-6) / 1e12 / FP64_NOMINAL_TFLOPS,
                      "traffic": APPLY_TRAFFIC_BYTES, "peak_source": "nominal FP64 (recipe table)",
-                     "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0>)" % npb,
+                     "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0,true>)" % npb,
                      "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
                      "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
                      "hbm_frac": achieved / peak},
         "e2e": {"value": ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
         "mixed_fp32_vcycle": mixed,
+        "paper_solver_gmres50_v03_tol1e-8": paper_solver,
         **extras,
         "gpu_launches": launches,
         "clocks": clocks,
