@@ -91,6 +91,11 @@ typedef struct {
                                the V-cycle as right preconditioner (Section 4; flexible form,
                                single-mesh handles only) */
   int32_t restart;          /* GMRES restart length m in [1, 512], default 50 (Section 5) */
+  int32_t autotune;         /* 1 (default): cdg_bind_device times the block-sparse kernel's
+                               variants (blocks in flight per step) on every level and keeps
+                               the fastest, and the first cdg_solve_multi does the same for the
+                               right-hand-side tile width and block rows per CTA; 0: fixed
+                               defaults.  Results are bit-identical either way. */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16
@@ -135,6 +140,15 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
 int cdg_batch_offsets(const cdg_handle* h, int32_t* n_meshes, int64_t* elem_offsets, int64_t* bface_offsets);
 const char* cdg_last_error(const cdg_handle* h);
 int cdg_query(const cdg_handle* h, cdg_info* info);
+/* Launch configuration chosen by the autotuner for one level (no counterpart in
+ * the paper; an execution detail of this library).  out[10]: [0] FP64 level-0
+ * apply and [1] FP64 level-0 residual (level 0 only), [2] V-cycle residual and
+ * [3] V-cycle smoother sweep (V-cycle precision): blocks in flight per step of
+ * the vector-load kernel; multi-right-hand-side kernels as (right-hand-side
+ * tile width, block rows per CTA): [4,5] smoother sweep, [6,7] residual,
+ * [8,9] FP64 level-0 apply (level 0 only).  0 = not applicable or not tuned
+ * yet.  Errors: CDG_EINVAL (bad level or NULL), CDG_ESTATE (not bound). */
+int cdg_tuning(const cdg_handle* h, int32_t level, int32_t* out);
 
 /* Quadrature points at which the caller samples f, g_D and g_N (R3: collapsed
  * Gauss-Legendre rules of degree 2p): xq [n_elements][nq][dim] in user order,

@@ -39,7 +39,7 @@ class cdg_options(C.Structure):
                 ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
-                ("krylov", C.c_int32), ("restart", C.c_int32)]
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("autotune", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -63,6 +63,7 @@ SIGNATURES = {
     "cdg_destroy": (None, [_P]),
     "cdg_last_error": (C.c_char_p, [_P]),
     "cdg_query": (_I32, [_P, _P]),
+    "cdg_tuning": (_I32, [_P, _I32, _P]),
     "cdg_quadrature_points": (_I32, [_P, _P, _P, _P]),
     "cdg_export_level": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P]),
     "cdg_export_agglomeration": (_I32, [_P, _I32, _P]),
@@ -135,7 +136,7 @@ class Solver:
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
-                 krylov: str = "cg", restart: int = 50):
+                 krylov: str = "cg", restart: int = 50, autotune: bool = True):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -153,7 +154,7 @@ class Solver:
         o.precision, o.switch_kind = PRECISION[precision], switch_kind
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
         o.nrhs = nrhs
-        o.krylov, o.restart = KRYLOV[krylov], restart
+        o.krylov, o.restart, o.autotune = KRYLOV[krylov], restart, int(autotune)
         arrs = {}
         if face_switch is not None:
             arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)
@@ -225,6 +226,18 @@ class Solver:
         aligned = (base + 255) & ~255
         self._check(lib().cdg_bind_device(self._h, aligned, nbytes, _stream_ptr(None)))
         return self
+
+    def tuning(self):
+        """Autotuned launch configuration per level (cdg_tuning)."""
+        keys = ("apply64_unroll", "residual64_unroll", "vcycle_residual_unroll", "vcycle_smoother_unroll",
+                "multi_smoother_tile", "multi_smoother_rows", "multi_residual_tile", "multi_residual_rows",
+                "multi_apply64_tile", "multi_apply64_rows")
+        out = []
+        for l in range(self.n_levels):
+            a = (C.c_int32 * 10)()
+            self._check(lib().cdg_tuning(self._h, l, a))
+            out.append({k: int(v) for k, v in zip(keys, a) if v})
+        return out
 
     def _dev(self, x):
         return _ptr(x)

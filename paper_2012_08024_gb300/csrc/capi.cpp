@@ -168,6 +168,7 @@ void cdg_default_options(cdg_options* o) {
   o->maxit = 500;
   o->krylov = 0;
   o->restart = 50;
+  o->autotune = 1;
 }
 
 const char* cdg_last_error(const cdg_handle* h) {
@@ -246,6 +247,19 @@ void cdg_destroy(cdg_handle* h) {
   if (!h) return;
   dev_release(h);
   delete h;
+}
+
+int cdg_tuning(const cdg_handle* h, int32_t level, int32_t* out) {
+  if (!h || !out) return CDG_EINVAL;
+  if (!h->dev) {
+    const_cast<cdg_handle*>(h)->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  if (level < 0 || level >= (int32_t)h->H.lev.size()) {
+    const_cast<cdg_handle*>(h)->err = "level out of range";
+    return CDG_EINVAL;
+  }
+  return dev_tuning(h, level, out);
 }
 
 int cdg_query(const cdg_handle* h, cdg_info* info) {

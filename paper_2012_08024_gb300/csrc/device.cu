@@ -194,8 +194,13 @@ struct VecLoad<double, NP> {
 // 3: y = x + omega (bh - x - Ahat x) with Ahat = D^{-1}(A - D) and bh = D^{-1} b,
 // i.e. one damped block-Jacobi step.  With dot != nullptr, MODE 0 also writes
 // the block partial of sum_i x_i y_i (for p^T A p).
-template <typename T, int NP, int MODE, bool VEC>
-__global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restrict__ rowptr,
+// VEC kernels keep UNR blocks of the row in flight per step (UNR is chosen per
+// level and mode by the autotuner at bind time; the summation order, block by
+// block and column by column, is the same for every UNR).  The register budget
+// grows with UNR (8 / UNR resident blocks of 256 threads per SM: 32, 64 or 128
+// registers), so the variants trade occupancy for loads in flight.
+template <typename T, int NP, int MODE, bool VEC, int UNR = 1>
+__global__ void __launch_bounds__(kThreads, 8 / UNR) bsr_kernel(int n, const int* __restrict__ rowptr,
                                                        const int* __restrict__ col, const T* __restrict__ A,
                                                        const T* __restrict__ Dinv, const T* __restrict__ x,
                                                        const T* __restrict__ b, T* __restrict__ y, T omega,
@@ -210,32 +215,35 @@ __global__ void __launch_bounds__(kThreads) bsr_kernel(int n, const int* __restr
   T acc = T(0);
   if (active) {
     const int b0 = rowptr[K], b1 = rowptr[K + 1];
-    for (int bb = b0; bb < b1; ++bb) {
-      const int J = ldg(col + bb);
-      const T* a = A + (size_t)bb * NP * NP + i * NP;
-      const T* xj = x + (size_t)J * NP;
-      if constexpr (VEC) {
-        // even n_p: the row of the block and x_J are 8-byte (FP32) / 16-byte
-        // (FP64) aligned runs, read as float2 / double2; two blocks per step
-        // keep twice the loads in flight
-        T av[NP], xv[NP];
-        VecLoad<T, NP>::load(a, av);
-        VecLoad<T, NP>::load(xj, xv);
-        if (bb + 1 < b1) {
-          const int J2 = ldg(col + bb + 1);
-          T av2[NP], xv2[NP];
-          VecLoad<T, NP>::load(a + NP * NP, av2);
-          VecLoad<T, NP>::load(x + (size_t)J2 * NP, xv2);
+    if constexpr (VEC) {
+      // even n_p: the row of the block and x_J are 8-byte (FP32) / 16-byte
+      // (FP64) aligned runs, read as float2 / double2; UNR blocks per step
+      // keep UNR times the loads in flight
+      int bb = b0;
+      for (; bb + UNR <= b1; bb += UNR) {
+        T av[UNR][NP], xv[UNR][NP];
 #pragma unroll
-          for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
-#pragma unroll
-          for (int j = 0; j < NP; ++j) acc = fma(av2[j], xv2[j], acc);
-          ++bb;
-        } else {
-#pragma unroll
-          for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+        for (int u = 0; u < UNR; ++u) {
+          const int J = ldg(col + bb + u);
+          VecLoad<T, NP>::load(A + (size_t)(bb + u) * NP * NP + i * NP, av[u]);
+          VecLoad<T, NP>::load(x + (size_t)J * NP, xv[u]);
         }
-      } else {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int j = 0; j < NP; ++j) acc = fma(av[u][j], xv[u][j], acc);
+      }
+      for (; bb < b1; ++bb) {
+        T av[NP], xv[NP];
+        VecLoad<T, NP>::load(A + (size_t)bb * NP * NP + i * NP, av);
+        VecLoad<T, NP>::load(x + (size_t)ldg(col + bb) * NP, xv);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
+      }
+    } else {
+      for (int bb = b0; bb < b1; ++bb) {
+        const T* a = A + (size_t)bb * NP * NP + i * NP;
+        const T* xj = x + (size_t)ldg(col + bb) * NP;
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
       }
@@ -631,25 +639,35 @@ inline unsigned rows_grid(int64_t nrows, int np) {
     default: return false;                                 \
   }
 
-// mode 0: y = A x (+ dot partials), 1: y = b - A x, 3: y = x + omega (bh - x - Ahat x)
+template <typename T, int NP, int MODE, int UNR>
+void launch_vec(unsigned g, cudaStream_t s, int n, const int* rowptr, const int* col, const T* A, const T* x,
+                const T* b, T* y, double omega, double* dot) {
+  launch(bsr_kernel<T, NP, MODE, true, UNR>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
+         (T)omega, MODE == 0 ? dot : (double*)nullptr);
+}
+
+template <typename T, int NP, int MODE>
+void launch_vec_unr(int unr, unsigned g, cudaStream_t s, int n, const int* rowptr, const int* col, const T* A,
+                    const T* x, const T* b, T* y, double omega, double* dot) {
+  if (unr >= 4) launch_vec<T, NP, MODE, 4>(g, s, n, rowptr, col, A, x, b, y, omega, dot);
+  else if (unr == 1) launch_vec<T, NP, MODE, 1>(g, s, n, rowptr, col, A, x, b, y, omega, dot);
+  else launch_vec<T, NP, MODE, 2>(g, s, n, rowptr, col, A, x, b, y, omega, dot);
+}
+
+// mode 0: y = A x (+ dot partials), 1: y = b - A x, 3: y = x + omega (bh - x - Ahat x).
+// unr: blocks in flight per step of the vector-load kernel (autotuned per level and mode).
 template <typename T>
 bool launch_bsr(int mode, int np, int n, const int* rowptr, const int* col, const T* A, const T* x, const T* b,
-                T* y, double omega, double* dot, cudaStream_t s, double* flag = nullptr) {
+                T* y, double omega, double* dot, cudaStream_t s, double* flag = nullptr, int unr = 2) {
   const unsigned g = rows_grid(n, np);
   // flag != nullptr marks vectors known to be 16-byte aligned: even n_p then
   // takes the vector-load kernel
   if (flag && np % 2 == 0) {
     CDG_NP_DISPATCH(np, {
       if constexpr (NP % 2 == 0) {
-        if (mode == 0)
-          launch(bsr_kernel<T, NP, 0, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
-                 (T)omega, dot);
-        else if (mode == 1)
-          launch(bsr_kernel<T, NP, 1, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
-                 (T)omega, (double*)nullptr);
-        else
-          launch(bsr_kernel<T, NP, 3, true>, g, kThreads, s, n, rowptr, col, A, (const T*)nullptr, x, b, y,
-                 (T)omega, (double*)nullptr);
+        if (mode == 0) launch_vec_unr<T, NP, 0>(unr, g, s, n, rowptr, col, A, x, b, y, omega, dot);
+        else if (mode == 1) launch_vec_unr<T, NP, 1>(unr, g, s, n, rowptr, col, A, x, b, y, omega, dot);
+        else launch_vec_unr<T, NP, 3>(unr, g, s, n, rowptr, col, A, x, b, y, omega, dot);
       }
     });
     return true;
@@ -730,6 +748,9 @@ const double* opL<double>(const DevLevel& L) { return L.L; }
 template <>
 const float* opL<float>(const DevLevel& L) { return L.L32; }
 
+template <typename T>
+int unr_of(const DevLevel& L, int mode) { return L.unr[sizeof(T) == 8 ? 0 : 1][mode]; }
+
 // One V(nu_pre, nu_post) cycle from a zero guess (R14) on levels 0..n, with
 // b0 / z0 the level-0 right-hand side and result (precision T).
 template <typename T>
@@ -755,11 +776,13 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     if (o.nu_pre >= 1) {
       if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, x, w, s)) return false;
       for (int k = 1; k < o.nu_pre; ++k) {
-        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s, D.scal + S_FLAG))
+        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s, D.scal + S_FLAG,
+                           unr_of<T>(L, 3)))
           return false;
         std::swap(x, t);
       }
-      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, D.scal + S_FLAG))
+      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, D.scal + S_FLAG,
+                         unr_of<T>(L, 1)))
         return false;
       if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), (const T*)L.r,
                               (T*)D.lev[l + 1].b, s))
@@ -789,7 +812,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     for (int k = 0; k < o.nu_post; ++k) {
       T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
       if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s,
-                         D.scal + S_FLAG))
+                         D.scal + S_FLAG, unr_of<T>(L, 3)))
         return false;
       if (out == t) std::swap(x, t);
       else x = out;
@@ -864,7 +887,7 @@ int dev_apply0(cdg_handle* h, int mode, const double* x, const double* b, double
   DeviceState& D = *h->dev;
   const DevLevel& L0 = D.lev[0];
   if (!launch_bsr<double>(mode, D.np, L0.n, L0.rowptr, L0.col, L0.A, x, b, y, h->opt.omega, nullptr, s,
-                          D.scal + S_FLAG)) {
+                          D.scal + S_FLAG, unr_of<double>(L0, mode))) {
     h->err = "unsupported number of basis functions per element";
     return CDG_EINVAL;
   }
@@ -964,6 +987,95 @@ void dev_release(cdg_handle* h) {
   h->dev = nullptr;
 }
 
+// Autotuner of the block-row tiling: times the vector-load block-sparse kernel
+// with 1, 2 and 4 blocks in flight per step for every (level, operator
+// precision, mode) that a solve launches, on the handle's own operators and
+// zero-filled work vectors, and keeps the fastest.  Every variant sums in the
+// same order, so the choice changes the timing only, never a result.
+static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
+  DeviceState& D = *h->dev;
+  if (D.np % 2 != 0) return CDG_OK;   // odd n_p: the scalar-load kernel has no variants
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  const double w = h->opt.omega;
+  double* flag = D.scal + S_FLAG;
+  auto pick = [&](auto&& launch_one) -> int {
+    int best = 2;
+    float tbest = 3.0e38f;
+    for (int u : {1, 2, 4}) {
+      const float t = time_calls(s, e0, e1, 3, [&] { launch_one(u); });
+      if (t < tbest) {
+        tbest = t;
+        best = u;
+      }
+    }
+    return best;
+  };
+  const int np = D.np;
+  // level 0, FP64: the outer apply and residual
+  {
+    DevLevel& L = D.lev[0];
+    const size_t nb = sizeof(double) * (size_t)D.ndofs;
+    cudaMemsetAsync(D.p, 0, nb, s);
+    cudaMemsetAsync(D.q, 0, nb, s);
+    cudaMemsetAsync(D.r, 0, nb, s);
+    L.unr[0][0] = pick([&](int u) {
+      launch_bsr<double>(0, np, L.n, L.rowptr, L.col, L.A, D.p, (const double*)nullptr, D.q, w, nullptr, s, flag, u);
+    });
+    L.unr[0][1] = pick([&](int u) {
+      launch_bsr<double>(1, np, L.n, L.rowptr, L.col, L.A, D.p, D.r, D.q, w, nullptr, s, flag, u);
+    });
+  }
+  // V-cycle levels in the V-cycle precision: residual and smoother sweep
+  auto tune_level = [&](auto zero, DevLevel& L, int l) {
+    using T = decltype(zero);
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    const size_t nb = sizeof(T) * (size_t)L.n * np;
+    T *x = (T*)L.x, *b = (T*)L.b, *bh = (T*)L.bh, *y = (T*)L.t;
+    cudaMemsetAsync(x, 0, nb, s);
+    cudaMemsetAsync(b, 0, nb, s);
+    cudaMemsetAsync(bh, 0, nb, s);
+    cudaMemsetAsync(y, 0, nb, s);
+    if (l > 0 || ti == 1)
+      L.unr[ti][1] = pick([&](int u) {
+        launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, y, w, nullptr, s, flag, u);
+      });
+    L.unr[ti][3] = pick([&](int u) {
+      launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, y, w, nullptr, s, flag, u);
+    });
+  };
+  for (int l = 0; l + 1 < D.nlev; ++l) {
+    if (D.precision == 0) tune_level(0.0, D.lev[l], l);
+    else tune_level(0.0f, D.lev[l], l);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  return CDG_OK;
+}
+
+int dev_tuning(const cdg_handle* h, int level, int32_t* out) {
+  for (int k = 0; k < 10; ++k) out[k] = 0;
+  const DeviceState& D = *h->dev;
+  const DevLevel& L = D.lev[level];
+  const bool vec = D.np % 2 == 0;
+  if (vec && level == 0) {
+    out[0] = L.unr[0][0];
+    out[1] = L.unr[0][1];
+  }
+  if (vec && level + 1 < D.nlev) {
+    const int ti = D.precision == 0 ? 0 : 1;
+    out[2] = L.unr[ti][1];
+    out[3] = L.unr[ti][3];
+  }
+  if (D.mr) mr_tuning(*D.mr, level, D.nlev, out);
+  return CDG_OK;
+}
+
 int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   const cdg::Hierarchy& H = h->H;
   const int prec = h->opt.precision == 2 ? 1 : h->opt.precision;
@@ -1050,6 +1162,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "bind");
+  if (h->opt.autotune) return autotune_bsr(h, s);
   return CDG_OK;
 }
 
@@ -1107,11 +1220,12 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)b) & 15) == 0;
   double* flag = aligned ? D.scal + S_FLAG : nullptr;
   if (op <= 1) {
-    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s, flag);
+    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s, flag,
+                            unr_of<double>(L, op));
   } else if (op == 2) {
     ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, (double*)L.bh, (double*)nullptr, h->opt.omega, s) &&
          launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)L.bh, y, h->opt.omega,
-                            nullptr, s, flag);
+                            nullptr, s, flag, unr_of<double>(L, 3));
   }
   else if (op == 3) ok = launch_restrict<double>(D.np, D.lev[level + 1].n, D.lev[level + 1].childptr, L.L, x, y, s);
   else ok = launch_prolong<double>(D.np, L.n, L.parent, L.L, x, y, true, s);
@@ -1143,12 +1257,12 @@ static int cg_part1(cdg_handle* h, cudaStream_t s) {
   if (D.nseg == 1) {
     const unsigned g = rows_grid(L0.n, D.np);
     launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, h->opt.omega,
-                       D.partial, s, D.scal + S_FLAG);
+                       D.partial, s, D.scal + S_FLAG, unr_of<double>(L0, 0));
     launch(finalize_kernel, 1u, kThreads, s, (const double*)D.partial, (int)g, D.npartial, 0, 0, h->opt.tol,
            D.scal);
   } else {
     launch_bsr<double>(0, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.p, (const double*)nullptr, D.q, h->opt.omega,
-                       (double*)nullptr, s, D.scal + S_FLAG);
+                       (double*)nullptr, s, D.scal + S_FLAG, unr_of<double>(L0, 0));
     int rc = dot_to(h, D.p, D.q, nullptr, 0, s);
     if (rc != CDG_OK) return rc;
   }
@@ -1237,7 +1351,8 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   const DevLevel& L0 = D.lev[0];
   if (use_u0) {
     launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, u_dev, D.x, 1);
-    launch_bsr<double>(1, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.x, D.bt, D.r, o.omega, nullptr, s, D.scal + S_FLAG);
+    launch_bsr<double>(1, D.np, L0.n, L0.rowptr, L0.col, L0.A, D.x, D.bt, D.r, o.omega, nullptr, s, D.scal + S_FLAG,
+                       unr_of<double>(L0, 1));
   } else {
     cudaMemsetAsync(D.x, 0, sizeof(double) * n, s);
     cudaMemcpyAsync(D.r, D.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);

@@ -35,39 +35,57 @@ struct Conv<__nv_bfloat16> {
   static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
+// the threads of one row group (threadIdx.y) copy ne values into shared memory
 template <typename TA, typename TC>
 __device__ __forceinline__ void stage_block(TC* s, const TA* a, int ne) {
   for (int t = threadIdx.x; t < ne; t += blockDim.x) s[t] = (TC)Conv<TA>::f(a[t]);
 }
 
-// y = A x (MODE 0), y = b - A x (1), y = x + omega (b - x - A x) (3; A = Ahat, b = D^-1 b)
-template <typename TA, typename TV, typename TC, int NP, int MODE>
-__global__ void mr_bsr_kernel(int R, const int* __restrict__ rowptr, const int* __restrict__ col,
+// y = A x (MODE 0), y = b - A x (1), y = x + omega (b - x - A x) (3; A = Ahat, b = D^-1 b).
+// A CTA of blockDim (TX, BR) owns BR consecutive block rows and one tile of TX
+// right-hand sides: row group threadIdx.y stages its blocks in shared memory
+// and thread x applies them to column blockIdx.y * TX + x.  TX and BR are the
+// autotuned right-hand-side tile width and block-row tiling; every choice sums
+// in the same order, so they change the timing only.
+template <typename TA, typename TV, typename TC, int NP, int MODE, int BR>
+__global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
                               const TA* __restrict__ A, const TV* __restrict__ x, const TV* __restrict__ b,
                               TV* __restrict__ y, TC omega) {
-  __shared__ TC as[NP * NP];
-  const int K = blockIdx.x;
-  const int r = threadIdx.x;
+  __shared__ TC as[BR][NP * NP];
+  const int K0 = blockIdx.x * BR;
+  const int K = K0 + threadIdx.y;
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  int b0 = 0, nb = 0, nbmax = 0;
+#pragma unroll
+  for (int q = 0; q < BR; ++q) {
+    if (K0 + q < n) {
+      const int a0 = rowptr[K0 + q], cnt = rowptr[K0 + q + 1] - a0;
+      nbmax = max(nbmax, cnt);
+      if (q == (int)threadIdx.y) {
+        b0 = a0;
+        nb = cnt;
+      }
+    }
+  }
   TC acc[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) acc[i] = TC(0);
-  const int b0 = rowptr[K], b1 = rowptr[K + 1];
-  for (int bb = b0; bb < b1; ++bb) {
+  for (int t = 0; t < nbmax; ++t) {
     __syncthreads();
-    stage_block<TA, TC>(as, A + (size_t)bb * NP * NP, NP * NP);
+    if (t < nb) stage_block<TA, TC>(as[threadIdx.y], A + (size_t)(b0 + t) * NP * NP, NP * NP);
     __syncthreads();
-    if (r < R) {
-      const TV* xj = x + (size_t)col[bb] * NP * R + r;
+    if (t < nb && r < R) {
+      const TV* xj = x + (size_t)col[b0 + t] * NP * R + r;
       TC xv[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) xv[j] = (TC)xj[(size_t)j * R];
 #pragma unroll
       for (int i = 0; i < NP; ++i)
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[i] = fma(as[i * NP + j], xv[j], acc[i]);
+        for (int j = 0; j < NP; ++j) acc[i] = fma(as[threadIdx.y][i * NP + j], xv[j], acc[i]);
     }
   }
-  if (r >= R) return;
+  if (K >= n || r >= R) return;
   const size_t base = (size_t)K * NP * R + r;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
@@ -297,7 +315,26 @@ struct MR {
   float *r32 = nullptr, *z32 = nullptr;
   double* scal = nullptr;      // [R][S_COUNT]
   double* partial = nullptr;   // [2G][R]
+  // autotuned (right-hand-side tile width, block rows per CTA) of mr_bsr_kernel per
+  // level and mode (0 FP64 level-0 apply, 1 residual, 3 smoother sweep); 0 = not tuned
+  int tile[kMaxLev][4] = {};
+  int rows[kMaxLev][4] = {};
+  bool tuned = false;
 };
+
+void mr_tuning(const MR& M, int level, int nlev, int32_t* out) {
+  if (!M.tuned) return;
+  if (level + 1 < nlev) {
+    out[4] = M.tile[level][3];
+    out[5] = M.rows[level][3];
+    out[6] = M.tile[level][1];
+    out[7] = M.rows[level][1];
+  }
+  if (level == 0) {
+    out[8] = M.tile[0][0];
+    out[9] = M.rows[0][0];
+  }
+}
 
 namespace {
 
@@ -402,7 +439,31 @@ namespace {
     default: return false;                                  \
   }
 
+// the same dispatch inside void lambdas (an unsupported n_p launches nothing)
+#define MR_NP_DISPATCH_V(NPV, ...)                          \
+  switch (NPV) {                                            \
+    case 3: { constexpr int NP = 3; __VA_ARGS__; break; }   \
+    case 4: { constexpr int NP = 4; __VA_ARGS__; break; }   \
+    case 6: { constexpr int NP = 6; __VA_ARGS__; break; }   \
+    case 10: { constexpr int NP = 10; __VA_ARGS__; break; } \
+    default: break;                                         \
+  }
+
 inline unsigned threads_for(int R) { return (unsigned)(((R + 31) / 32) * 32); }
+
+// mr_bsr_kernel with a right-hand-side tile of tx columns and br block rows per CTA
+template <typename TA, typename TV, typename TC, int NP, int MODE>
+void mr_bsr_launch(int tx, int br, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
+                   const TV* b, TV* y, TC omega, cudaStream_t s) {
+  const dim3 grid((unsigned)((n + br - 1) / br), (unsigned)((R + tx - 1) / tx)), block((unsigned)tx, (unsigned)br);
+  if (br >= 4) mr_bsr_kernel<TA, TV, TC, NP, MODE, 4><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
+  else if (br == 2) mr_bsr_kernel<TA, TV, TC, NP, MODE, 2><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
+  else mr_bsr_kernel<TA, TV, TC, NP, MODE, 1><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
+  count_launch();
+}
+
+inline int tile_of(const MR& M, int l, int mode) { return M.tile[l][mode] ? M.tile[l][mode] : (int)threads_for(M.R); }
+inline int rows_of(const MR& M, int l, int mode) { return M.rows[l][mode] ? M.rows[l][mode] : 1; }
 
 template <typename TA>
 bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, float* z0, cudaStream_t s) {
@@ -412,13 +473,13 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
   auto bsr = [&](int mode, int l, const int* rp, const int* cl, const void* A, const float* x, const float* b,
                  float* y) -> bool {
     const int n = D.lev[l].n;
+    const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode);
     MR_NP_DISPATCH(np, {
       if (mode == 1)
-        mr_bsr_kernel<float, float, float, NP, 1><<<n, T, 0, s>>>(R, rp, cl, (const float*)A, x, b, y, w);
+        mr_bsr_launch<float, float, float, NP, 1>(tx, br, n, R, rp, cl, (const float*)A, x, b, y, w, s);
       else
-        mr_bsr_kernel<TA, float, float, NP, 3><<<n, T, 0, s>>>(R, rp, cl, (const TA*)A, x, b, y, w);
+        mr_bsr_launch<TA, float, float, NP, 3>(tx, br, n, R, rp, cl, (const TA*)A, x, b, y, w, s);
     });
-    count_launch();
     return true;
   };
   if (nlev == 1) {
@@ -489,11 +550,71 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
 
 bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t s) {
   const DevLevel& L0 = D.lev[0];
-  const unsigned T = threads_for(M.R);
-  MR_NP_DISPATCH(D.np, mr_bsr_kernel<double, double, double, NP, 0><<<L0.n, T, 0, s>>>(
-                           M.R, L0.rowptr, L0.col, L0.A, x, (const double*)nullptr, y, 0.0));
-  count_launch();
+  const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0);
+  MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, L0.n, M.R, L0.rowptr, L0.col, L0.A, x,
+                                                                     (const double*)nullptr, y, 0.0, s)));
   return true;
+}
+
+// Autotuner of the multi-right-hand-side block-sparse kernel: for every level
+// and mode the solve launches, times the (tile width, block rows per CTA)
+// pairs with tile width in {32, ..., 1024} up to the padded R and at most 1024
+// threads per CTA, on the handle's operators and zero-filled work vectors, and
+// keeps the fastest.
+template <typename TA>
+bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
+  const int np = D.np, nlev = D.nlev, R = M.R;
+  const int tmax = (int)threads_for(R);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return false;
+  auto pick = [&](int l, int mode, auto&& launch_one) {
+    float tbest = 3.0e38f;
+    for (int tx = 32; tx <= 1024; tx *= 2) {
+      if (tx > tmax && tx != 32) break;
+      for (int br : {1, 2, 4}) {
+        if (tx * br > 1024) continue;
+        const float t = time_calls(s, e0, e1, 2, [&] { launch_one(tx, br); });
+        if (t < tbest) {
+          tbest = t;
+          M.tile[l][mode] = tx;
+          M.rows[l][mode] = br;
+        }
+      }
+    }
+  };
+  bool ok = true;
+  {
+    const DevLevel& L0 = D.lev[0];
+    const size_t nv = (size_t)L0.n * np * R;
+    cudaMemsetAsync(M.p, 0, nv * sizeof(double), s);
+    pick(0, 0, [&](int tx, int br) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, L0.n, R, L0.rowptr, L0.col, L0.A,
+                                                                         (const double*)M.p, (const double*)nullptr,
+                                                                         M.q, 0.0, s)));
+    });
+  }
+  const float w = (float)omega;
+  for (int l = 0; l + 1 < nlev; ++l) {
+    const DevLevel& DL = D.lev[l];
+    MRLevel& L = M.lev[l];
+    const size_t nv = (size_t)DL.n * np * R;
+    for (float* v : {L.x, L.b, L.bh, L.t}) cudaMemsetAsync(v, 0, nv * sizeof(float), s);
+    pick(l, 1, [&](int tx, int br) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<float, float, float, NP, 1>(tx, br, DL.n, R, DL.rowptr, DL.col,
+                                                                      (const float*)L.A, (const float*)L.x,
+                                                                      (const float*)L.b, L.t, w, s)));
+    });
+    pick(l, 3, [&](int tx, int br) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<TA, float, float, NP, 3>(tx, br, DL.n, R, DL.hrowptr, DL.hcol,
+                                                                   (const TA*)L.Ahat, (const float*)L.x,
+                                                                   (const float*)L.bh, L.t, w, s)));
+    });
+  }
+  ok = cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  M.tuned = ok;
+  return ok;
 }
 
 void mr_dot(DeviceState& D, MR& M, const double* x, const double* y, const double* w, int which, double tol,
@@ -526,8 +647,15 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   const size_t nrows = (size_t)D.ne * D.np;
   const unsigned T = threads_for(R);
   const unsigned gv = 4 * 152;
-  cudaMemsetAsync(M.scal, 0, sizeof(double) * (size_t)R * S_COUNT, s);
   bool ok = true;
+  if (o.autotune && !M.tuned) {
+    ok = M.bf16 ? mr_autotune<__nv_bfloat16>(D, M, o.omega, s) : mr_autotune<float>(D, M, o.omega, s);
+    if (!ok) {
+      h->err = "cdg_solve_multi: autotuning failed (unsupported n_p or a CUDA error)";
+      return CDG_ECUDA;
+    }
+  }
+  cudaMemsetAsync(M.scal, 0, sizeof(double) * (size_t)R * S_COUNT, s);
   MR_NP_DISPATCH(D.np, mr_rhs_kernel<NP><<<(unsigned)D.ne, T, 0, s>>>(R, D.nq, (int)D.ne, D.perm0, D.rhs_vol, f_q, M.bt));
   count_launch();
   cudaMemsetAsync(M.x, 0, sizeof(double) * nv, s);

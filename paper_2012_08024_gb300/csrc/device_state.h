@@ -33,6 +33,9 @@ struct DevLevel {
   double* Ahat = nullptr;
   float* Ahat32 = nullptr;
   int64_t hnnzb = 0;
+  // autotuned blocks in flight per step of the vector-load block-sparse kernel,
+  // [0] FP64 / [1] FP32 operator, by mode (0 apply, 1 residual, 3 smoother)
+  int unr[2][4] = {{2, 2, 2, 2}, {2, 2, 2, 2}};
   void* bh = nullptr;        // D^{-1} b of the current V-cycle visit
   void* x = nullptr;         // V-cycle work vectors in the V-cycle precision
   void* t = nullptr;
@@ -117,6 +120,20 @@ struct GmLayout {
 };
 enum GmMisc { GM_WN0 = 0, GM_WN1, GM_HNEXT, GM_REORTH, GM_J };
 
+// Autotuning helper: average time in ms of `reps` calls of fn on stream s,
+// after one untimed call.
+template <typename F>
+float time_calls(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& fn) {
+  fn();
+  cudaEventRecord(e0, s);
+  for (int k = 0; k < reps; ++k) fn();
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
 // launch counter shared by all translation units
 void count_launch(long long n = 1);
 long long launch_count();
@@ -141,3 +158,4 @@ MR* mr_new();
 void mr_delete(MR* m);
 size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off);
 void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s);
+void mr_tuning(const MR& M, int level, int nlev, int32_t* out);

@@ -32,3 +32,4 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
 int dev_adjoint(cdg_handle* h, int what, const double* lam_user, const double* u_user, const double* gD,
                 double* out, void* stream);
 int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int* iters, void* stream);
+int dev_tuning(const cdg_handle* h, int level, int32_t* out);
