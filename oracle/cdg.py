@@ -53,6 +53,18 @@ class Level0:
         self.vrule = simplex_rule(d, 2 * p)
         self.frule = simplex_rule(d - 1, 2 * p)
 
+    def with_degree(self, q: int) -> "Level0":
+        """The same discretisation (mesh, switch, C_D, kappa) at degree q: the
+        rediscretised operators of the p-multigrid levels (Section 4.4)."""
+        other = Level0.__new__(Level0)
+        other.topo, other.p, other.d = self.topo, q, self.d
+        other.bases = [Basis([self.topo.simplex(K)], q) for K in range(self.topo.ne)]
+        other.np_ = len(other.bases[0].exps)
+        other.C_D, other.kappa = self.C_D, self.kappa
+        other.vrule = simplex_rule(self.d, 2 * q)
+        other.frule = simplex_rule(self.d - 1, 2 * q)
+        return other
+
     # ---- quadrature points (the points at which the caller samples f, g_D, g_N)
     def volume_points(self, K):
         return map_simplex(self.topo.simplex(K), *self.vrule)

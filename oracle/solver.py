@@ -20,17 +20,21 @@ import scipy.sparse as sp
 
 
 class VCycle:
-    def __init__(self, A: list, L: list, npb: int, nu1: int = 1, nu2: int = 1,
+    def __init__(self, A: list, L: list, npb, nu1: int = 1, nu2: int = 1,
                  omega: float = 2.0 / 3.0, R: list | None = None):
-        self.A, self.L, self.npb = A, L, npb
+        """npb: basis functions per element, one value for every level or a
+        list with one value per level (p-multigrid levels)."""
+        self.A, self.L = A, L
+        self.npbs = list(npb) if hasattr(npb, "__len__") else [npb] * len(A)
+        self.npb = self.npbs[0]
         self.R = R if R is not None else [Li.T.tocsr() for Li in L]
         self.nu1, self.nu2, self.omega = nu1, nu2, omega
         self.Dinv = []
-        for Al in A[:-1]:
-            n = Al.shape[0] // npb
+        for Al, npl in zip(A[:-1], self.npbs):
+            n = Al.shape[0] // npl
             blocks = []
             for K in range(n):
-                sl = slice(K * npb, (K + 1) * npb)
+                sl = slice(K * npl, (K + 1) * npl)
                 blocks.append(np.linalg.inv(Al[sl, sl].toarray()))
             self.Dinv.append(sp.block_diag(blocks, format="csr"))
         self.coarse = np.linalg.inv(A[-1].toarray())

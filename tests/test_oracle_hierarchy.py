@@ -18,13 +18,15 @@ from oracle.quadrature import simplex_rule, map_simplex
 from synthetic import jittered_square, kuhn_cube
 
 
-@pytest.fixture(scope="module", params=["tri", "tet"])
+@pytest.fixture(scope="module", params=["tri", "tet", "tri_pmg", "tet_pmg"])
 def hier(request):
     if request.param == "tri":
-        L0 = Level0(jittered_square(6, neumann_axes=(0,)), 2)
-    else:
-        L0 = Level0(kuhn_cube(2), 1)
-    return MGHierarchy(L0, max_levels=4, seed=3)
+        return MGHierarchy(Level0(jittered_square(6, neumann_axes=(0,)), 2), max_levels=4, seed=3)
+    if request.param == "tet":
+        return MGHierarchy(Level0(kuhn_cube(2), 1), max_levels=4, seed=3)
+    if request.param == "tri_pmg":    # p = 3, 2, 1 on the fine mesh, then agglomeration at p = 1
+        return MGHierarchy(Level0(jittered_square(5, neumann_axes=(0,)), 3), max_levels=3, seed=3, pmg=True)
+    return MGHierarchy(Level0(kuhn_cube(2), 2), max_levels=3, seed=3, pmg=True)
 
 
 def test_mass_identity_and_transfer(hier):
@@ -52,9 +54,9 @@ def _direct_ldg_gradient(hier, l):
     fine Neumann faces; faces inside an agglomerate drop out."""
     L0 = hier.lvl0
     t = L0.topo
-    d, npb = hier.d, hier.np_
+    d, npb = hier.d, hier.nps[l]
     owner = np.zeros(t.ne, dtype=int)
-    for E, mem in enumerate(hier.agg.members[l]):
+    for E, mem in enumerate(hier.members[l]):
         owner[mem] = E
     B = hier.bases[l]
     nE = len(B)
@@ -92,18 +94,20 @@ def _direct_ldg_gradient(hier, l):
 def _direct_injection(hier, l):
     L0 = hier.lvl0
     t = L0.topo
-    npb = hier.np_
-    P = np.zeros((t.ne * npb, len(hier.bases[l]) * npb))
+    npb, npl = hier.np_, hier.nps[l]
+    P = np.zeros((t.ne * npb, len(hier.bases[l]) * npl))
     rp, rw = L0.vrule
-    for E, mem in enumerate(hier.agg.members[l]):
+    for E, mem in enumerate(hier.members[l]):
         for K in mem:
             x, w = map_simplex(t.simplex(K), rp, rw)
-            P[K * npb:(K + 1) * npb, E * npb:(E + 1) * npb] = \
+            P[K * npb:(K + 1) * npb, E * npl:(E + 1) * npl] = \
                 (L0.bases[K].eval(x) * w[:, None]).T @ hier.bases[l][E].eval(x)
     return P
 
 
 def test_coarse_operator_independent_route(hier):
+    if hier.n_plevels:
+        pytest.skip("p-multigrid levels are rediscretised; their agglomeration part is the p = 1 hierarchy")
     C0 = hier.C[0].toarray()
     for l in range(1, hier.n_levels):
         Gd = _direct_ldg_gradient(hier, l)
