@@ -445,6 +445,31 @@ def main():
                 del Sg
         except Exception as e:
             paper_solver["error"] = repr(e)[:300]
+    # ---- the same solve with the p-multigrid front end (Section 4.4): degrees p..2 on the
+    # fine mesh before the agglomeration levels (built at p = 1)
+    pmg_line = None
+    if args.extras and prec == "fp64" and p > 1:
+        pmg_line = {}
+        try:
+            for pr in ("fp64", "fp32"):
+                Sp = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=pr, tol=1e-10,
+                                maxit=500, pmg=True).bind(dev)
+                for _ in range(2):
+                    up, hp, itp, rcp = Sp.solve(fq)
+                barrier()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    up, hp, itp, rcp = Sp.solve(fq)
+                e1.record(stream)
+                barrier()
+                msp = e0.elapsed_time(e1) / args.steps
+                pmg_line["vcycle_" + pr] = {
+                    "value": ndof * ws / (msp * 1e-3), "unit": "DOF/s", "ms_per_step": msp, "iterations": itp,
+                    "levels": Sp.n_levels, "np_l": Sp.info["np_l"], "rc": rcp, "final_rel_residual": float(hp[-1]),
+                    "speedup_vs_fp64_headline": ms / msp}
+                del Sp
+        except Exception as e:
+            pmg_line["error"] = repr(e)[:300]
     extras = {}
     if args.extras and prec == "fp64":
         try:
@@ -479,6 +504,7 @@ def main():
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
         "mixed_fp32_vcycle": mixed,
         "paper_solver_gmres50_v03_tol1e-8": paper_solver,
+        "pmg_front_end": pmg_line,
         **extras,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -91,6 +91,11 @@ typedef struct {
                                the V-cycle as right preconditioner (Section 4; flexible form,
                                single-mesh handles only) */
   int32_t restart;          /* GMRES restart length m in [1, 512], default 50 (Section 5) */
+  int32_t pmg;              /* 1: p-multigrid front end (Section 4.4): the levels of degree p,
+                               p-1, ..., 2 on the fine mesh (CDG rediscretised at each degree,
+                               truncation transfers) come before the agglomeration hierarchy,
+                               built at p = 1 with max_levels levels; not with nrhs or batched
+                               handles.  Default 0. */
   int32_t autotune;         /* 1 (default): cdg_bind_device times the block-sparse kernel's
                                variants (blocks in flight per step) on every level and keeps
                                the fastest, and the first cdg_solve_multi does the same for the
@@ -111,6 +116,8 @@ typedef struct {
   int64_t device_bytes;     /* size of the buffer cdg_bind_device needs */
   double setup_seconds[4];  /* mesh, level-0 assembly, agglomeration, coarsening */
   int32_t n_meshes;         /* 1, or the number of meshes of a batched handle */
+  int32_t np_l[CDG_MAX_LEVELS];   /* basis functions per element on each level */
+  int32_t n_plevels;        /* p-multigrid: levels of degree p..2 on the fine mesh (0 without) */
 } cdg_info;
 
 /* Defaults: p=2, gamma=1e4, V(1,1), omega=2/3, 4 levels, seed 0, FP64,
@@ -159,8 +166,10 @@ int cdg_quadrature_points(const cdg_handle* h, double* xq, double* xbq, int32_t*
 /* Host copies of the set-up, for inspection and tests (any pointer may be
  * NULL).  perm [n_l]: tree position -> working index (level 0: user element);
  * parent [n_l] (tree order, -1 on the coarsest level); A_l in tree order as
- * BSR: rowptr [n_l+1], col [nnzb_l], val [nnzb_l][n_p][n_p] row-major blocks;
- * transfer blocks L [n_l][n_p][n_p] with L_K = int_K phi_K psi_parent^T. */
+ * BSR: rowptr [n_l+1], col [nnzb_l], val [nnzb_l][n_p(l)][n_p(l)] row-major
+ * blocks; transfer blocks L [n_l][n_p(l)][n_p(l+1)] with
+ * L_K = int_K phi_K psi_parent^T (between two degrees of a p-multigrid
+ * hierarchy: the truncation [I; 0]).  n_p(l) is cdg_info.np_l[l]. */
 int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t* parent,
                      int64_t* rowptr, int32_t* col, double* val, double* L);
 /* Agglomeration of one level in working numbering (Algorithm 2 output):

@@ -39,7 +39,7 @@ class cdg_options(C.Structure):
                 ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
-                ("krylov", C.c_int32), ("restart", C.c_int32), ("autotune", C.c_int32)]
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -48,7 +48,8 @@ class cdg_info(C.Structure):
                 ("n_interior_faces", C.c_int64), ("n_bfaces", C.c_int64), ("n_dofs", C.c_int64),
                 ("n_l", C.c_int64 * CDG_MAX_LEVELS), ("nnzb_l", C.c_int64 * CDG_MAX_LEVELS),
                 ("h_avg", C.c_double), ("C_D", C.c_double), ("device_bytes", C.c_int64),
-                ("setup_seconds", C.c_double * 4), ("n_meshes", C.c_int32)]
+                ("setup_seconds", C.c_double * 4), ("n_meshes", C.c_int32),
+                ("np_l", C.c_int32 * CDG_MAX_LEVELS), ("n_plevels", C.c_int32)]
 
 
 _lib = None
@@ -136,7 +137,7 @@ class Solver:
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
-                 krylov: str = "cg", restart: int = 50, autotune: bool = True):
+                 krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -155,6 +156,7 @@ class Solver:
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
         o.nrhs = nrhs
         o.krylov, o.restart, o.autotune = KRYLOV[krylov], restart, int(autotune)
+        o.pmg = int(pmg)
         arrs = {}
         if face_switch is not None:
             arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)
@@ -174,7 +176,7 @@ class Solver:
         self.buffer = None
         inf = cdg_info()
         L.cdg_query(h, C.byref(inf))
-        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l") else
+        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l", "np_l") else
                          list(getattr(inf, k)) if k == "setup_seconds" else getattr(inf, k))
                      for k, _ in cdg_info._fields_}
         self.np_ = inf.n_p
@@ -204,10 +206,11 @@ class Solver:
     def export_level(self, level: int):
         n = self.info["n_l"][level]
         nnzb = self.info["nnzb_l"][level]
-        npb = self.np_
+        npb = self.info["np_l"][level]
+        npc = self.info["np_l"][level + 1] if level + 1 < self.n_levels else npb
         out = dict(perm=np.empty(n, dtype=np.int64), parent=np.empty(n, dtype=np.int32),
                    rowptr=np.empty(n + 1, dtype=np.int64), col=np.empty(nnzb, dtype=np.int32),
-                   val=np.empty((nnzb, npb, npb)), L=np.zeros((n, npb, npb)))
+                   val=np.empty((nnzb, npb, npb)), L=np.zeros((n, npb, npc)))
         self._check(lib().cdg_export_level(self._h, level, *(out[k].ctypes.data for k in
                                                              ("perm", "parent", "rowptr", "col", "val", "L"))))
         return out
@@ -387,7 +390,7 @@ class BatchSolver(Solver):
         self.buffer = None
         inf = cdg_info()
         L.cdg_query(h, C.byref(inf))
-        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l") else
+        self.info = {k: (list(getattr(inf, k))[:inf.n_levels] if k in ("n_l", "nnzb_l", "np_l") else
                          list(getattr(inf, k)) if k == "setup_seconds" else getattr(inf, k))
                      for k, _ in cdg_info._fields_}
         self.np_ = inf.n_p

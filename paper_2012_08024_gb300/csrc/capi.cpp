@@ -38,6 +38,11 @@ static int check_options(const cdg_options* opt) {
   if (opt->krylov < 0 || opt->krylov > 1) return fail(nullptr, CDG_EINVAL, "krylov must be 0 (CG) or 1 (GMRES)");
   if (opt->krylov == 1 && (opt->restart < 1 || opt->restart > 512))
     return fail(nullptr, CDG_EINVAL, "GMRES restart must be in [1, 512]");
+  if (opt->pmg < 0 || opt->pmg > 1) return fail(nullptr, CDG_EINVAL, "pmg must be 0 or 1");
+  if (opt->pmg && opt->p > 1 && opt->max_levels + opt->p - 1 > CDG_MAX_LEVELS)
+    return fail(nullptr, CDG_EINVAL, "p-multigrid: max_levels + p - 1 must be at most 16");
+  if (opt->pmg && opt->p > 1 && opt->nrhs)
+    return fail(nullptr, CDG_EINVAL, "p-multigrid is not available with nrhs (cdg_solve_multi)");
   return CDG_OK;
 }
 
@@ -55,6 +60,7 @@ static int check_mesh(const cdg_mesh* mesh) {
 static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arrays, cdg::Hierarchy& H) {
   cdg::Options& o = H.opt;
   o.p = opt->p;
+  o.pmg = opt->pmg;
   o.gamma = opt->gamma;
   o.nu_pre = opt->nu_pre;
   o.nu_post = opt->nu_post;
@@ -87,6 +93,37 @@ static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arr
   double t1 = now();
   cdg::build_level0(H);
   double t2 = now();
+  if (o.pmg && o.p > 1) {
+    // p-multigrid (Section 4.4): the same discretisation at degrees p-1, ..., 2, then
+    // the complete degree-1 hierarchy
+    std::vector<cdg::Hierarchy> fine(o.p - 2);
+    for (int q = o.p - 1; q >= 2; --q) {
+      cdg::Hierarchy& F = fine[o.p - 1 - q];
+      F.opt = o;
+      F.opt.p = q;
+      F.mesh = H.mesh;
+      F.mono.init(mesh->dim, q);
+      F.np = F.mono.np;
+      F.vrule = cdg::simplex_rule(mesh->dim, 2 * q);
+      F.frule = cdg::simplex_rule(mesh->dim - 1, 2 * q);
+      F.lev.assign(1, cdg::Level());
+      cdg::build_level0(F);
+    }
+    cdg_options o1 = *opt;
+    o1.p = 1;
+    o1.pmg = 0;
+    cdg::Hierarchy H1;
+    build_one(mesh, &o1, use_arrays, H1);
+    double t3 = now();
+    cdg::merge_pmg(H, fine, H1);
+    cdg::build_rhs_data(H);
+    double t4 = now();
+    H.t_mesh = t1 - t0;
+    H.t_assemble = t2 - t1 + (t3 - t2) - H1.t_agglomerate - H1.t_coarsen;
+    H.t_agglomerate = H1.t_agglomerate;
+    H.t_coarsen = H1.t_coarsen + (t4 - t3);
+    return;
+  }
   cdg::agglomerate(H);
   double t3 = now();
   cdg::coarsen(H);
@@ -200,6 +237,7 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
   if (opt->kappa || opt->face_switch || opt->enumeration || opt->nrhs)
     return fail(nullptr, CDG_EINVAL, "per-element arrays and nrhs are not supported for batched handles");
   if (opt->krylov != 0) return fail(nullptr, CDG_EINVAL, "batched handles solve with CG (krylov = 0)");
+  if (opt->pmg != 0) return fail(nullptr, CDG_EINVAL, "p-multigrid is not available for batched handles");
   int rc = check_options(opt);
   for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
   if (rc != CDG_OK) return rc;
@@ -290,6 +328,8 @@ int cdg_query(const cdg_handle* h, cdg_info* info) {
   info->setup_seconds[2] = H.t_agglomerate;
   info->setup_seconds[3] = H.t_coarsen;
   info->n_meshes = (int32_t)H.seg_rows[0].size() - 1;
+  for (size_t l = 0; l < H.lev.size(); ++l) info->np_l[l] = H.np_l.empty() ? H.np : H.np_l[l];
+  info->n_plevels = H.n_plevels;
   return CDG_OK;
 }
 
@@ -317,15 +357,24 @@ int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t*
   if (level < 0 || level >= (int32_t)H.lev.size()) return CDG_EINVAL;
   const int64_t n = H.lev[level].n;
   const cdg::BSR& A = H.A_t[level];
-  const size_t nb2 = (size_t)H.np * H.np;
   const bool last = level + 1 == (int32_t)H.lev.size();
+  const int npf = H.np_l[level], npc = last ? npf : H.np_l[level + 1];
+  const size_t nb2 = (size_t)npf * npc;
   if (perm) std::memcpy(perm, H.order[level].data(), sizeof(int64_t) * n);
   if (parent)
     for (int64_t k = 0; k < n; ++k) parent[k] = last ? -1 : H.parent_t[level][k];
   if (rowptr) std::memcpy(rowptr, A.rowptr.data(), sizeof(int64_t) * (n + 1));
   if (col) std::memcpy(col, A.col.data(), sizeof(int32_t) * A.col.size());
   if (val) std::memcpy(val, A.val.data(), sizeof(double) * A.val.size());
-  if (L && !last) std::memcpy(L, H.L_t[level].data(), sizeof(double) * n * nb2);
+  if (L && !last) {
+    if (H.L_t[level].empty()) {   // between two degrees: truncation of the nested bases
+      std::memset(L, 0, sizeof(double) * n * nb2);
+      for (int64_t k = 0; k < n; ++k)
+        for (int i = 0; i < npc; ++i) L[k * nb2 + (size_t)i * npc + i] = 1.0;
+    } else {
+      std::memcpy(L, H.L_t[level].data(), sizeof(double) * n * nb2);
+    }
+  }
   return CDG_OK;
 }
 

@@ -44,7 +44,6 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
               int gmres_m) {
   Carver c{base};
   const int np = H.np;
-  const size_t nb2 = (size_t)np * np;
   const int nlev = (int)H.lev.size();
   const int64_t ne = H.mesh.ne;
   const size_t vecbytes_elems = (size_t)ne * np;
@@ -64,7 +63,11 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   for (int l = 0; l < nlev; ++l) {
     DevLevel& L = D.lev[l];
     const cdg::BSR& A = H.A_t[l];
+    const int npl = H.np_l.empty() ? np : H.np_l[l];
+    const size_t nb2l = (size_t)npl * npl;
     L.n = (int)A.nrows;
+    L.np = npl;
+    L.ptrans = l + 1 < nlev && H.L_t[l].empty();
     L.nnzb = A.nnzb();
     L.rowptr = c.take<int>(A.nrows + 1);
     L.col = c.take<int>(A.nnzb());
@@ -76,27 +79,29 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
       L.hnnzb = Sh.nnzb();
       L.hrowptr = c.take<int>(Sh.nrows + 1);
       L.hcol = c.take<int>(Sh.nnzb() + 1);
+      // transfer blocks between agglomeration levels only (degree steps truncate)
+      const size_t nL = H.L_t[l].size();
       if (precision == 0) {
-        L.Dinv = c.take<double>((size_t)L.n * nb2);
-        L.L = c.take<double>((size_t)L.n * nb2);
+        L.Dinv = c.take<double>((size_t)L.n * nb2l);
+        if (nL) L.L = c.take<double>(nL);
         L.Ahat = c.take<double>(Sh.val.size() + 1);
       } else {
         L.A32 = c.take<float>(A.val.size());
-        L.Dinv32 = c.take<float>((size_t)L.n * nb2);
-        L.L32 = c.take<float>((size_t)L.n * nb2);
+        L.Dinv32 = c.take<float>((size_t)L.n * nb2l);
+        if (nL) L.L32 = c.take<float>(nL);
         L.Ahat32 = c.take<float>(Sh.val.size() + 1);
       }
       L.parent = c.take<int>(L.n);
     }
     if (l > 0) L.childptr = c.take<int>(L.n + 1);
-    const size_t nv = (size_t)L.n * np;
+    const size_t nv = (size_t)L.n * npl;
     L.x = c.take<char>(nv * vsz);
     L.t = c.take<char>(nv * vsz);
     L.r = c.take<char>(nv * vsz);
     L.b = c.take<char>(nv * vsz);
     L.bh = c.take<char>(nv * (l == 0 ? sizeof(double) : vsz));
   }
-  D.nc = (int)(H.lev.back().n * np);
+  D.nc = (int)(H.lev.back().n * D.lev[nlev - 1].np);
   D.nseg = (int)H.seg_rows[0].size() - 1;
   D.bps = std::max(1, kDotBlocks / D.nseg);
   D.seg_dof = c.take<long long>(D.nseg + 1);
@@ -352,6 +357,33 @@ __global__ void coarse_kernel(int nc, const int* __restrict__ crow_seg, const in
   for (int j = lane; j < nm; j += 32) s = fma(a[j], (double)bm[j], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (TO)s;
+}
+
+// Between two degrees of the p-multigrid levels (Section 4.4) the orthonormal
+// bases are nested: the degree q-1 basis is the first npc functions of the
+// degree q basis on the same element, so restriction keeps the first npc
+// coefficients of every element and prolongation adds them back (ADD) or
+// writes them with zero higher coefficients.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ptrunc_restrict_kernel(int n, int npf, int npc,
+                                                                   const T* __restrict__ r, T* __restrict__ bc) {
+  const size_t tot = (size_t)n * npc;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t K = t / npc;
+    bc[t] = r[K * npf + (t - K * npc)];
+  }
+}
+
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(kThreads) ptrunc_prolong_kernel(int n, int npf, int npc,
+                                                                  const T* __restrict__ xc, T* __restrict__ x) {
+  const size_t tot = (size_t)n * npf;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t K = t / npf;
+    const int i = (int)(t - K * npf);
+    const T v = i < npc ? xc[K * npc + i] : T(0);
+    x[t] = ADD ? x[t] + v : v;
+  }
 }
 
 template <typename TI, typename TO>
@@ -712,6 +744,31 @@ bool launch_prolong(int np, int n, const int* parent, const T* L, const T* xc, T
 
 unsigned vec_grid(size_t n) { return (unsigned)std::min<size_t>(kDotBlocks, (n + kThreads - 1) / kThreads + 1); }
 
+// restriction / prolongation between levels l and l+1: transfer blocks between
+// agglomeration levels, truncation between two degrees on the same elements
+template <typename T>
+bool transfer_restrict(const DeviceState& D, int l, const T* Lb, const T* r, T* bc, cudaStream_t s) {
+  const DevLevel& F = D.lev[l];
+  const DevLevel& C = D.lev[l + 1];
+  if (F.ptrans) {
+    launch(ptrunc_restrict_kernel<T>, vec_grid((size_t)C.n * C.np), kThreads, s, C.n, F.np, C.np, r, bc);
+    return true;
+  }
+  return launch_restrict<T>(F.np, C.n, C.childptr, Lb, r, bc, s);
+}
+
+template <typename T>
+bool transfer_prolong(const DeviceState& D, int l, const T* Lb, const T* xc, T* x, bool add, cudaStream_t s) {
+  const DevLevel& F = D.lev[l];
+  const DevLevel& C = D.lev[l + 1];
+  if (F.ptrans) {
+    if (add) launch(ptrunc_prolong_kernel<T, true>, vec_grid((size_t)F.n * F.np), kThreads, s, F.n, F.np, C.np, xc, x);
+    else launch(ptrunc_prolong_kernel<T, false>, vec_grid((size_t)F.n * F.np), kThreads, s, F.n, F.np, C.np, xc, x);
+    return true;
+  }
+  return launch_prolong<T>(F.np, F.n, F.parent, Lb, xc, x, add, s);
+}
+
 int cuda_fail(cdg_handle* h, cudaError_t e, const char* where) {
   h->err = std::string(where) + ": " + cudaGetErrorString(e);
   return CDG_ECUDA;
@@ -755,7 +812,6 @@ int unr_of(const DevLevel& L, int mode) { return L.unr[sizeof(T) == 8 ? 0 : 1][m
 // b0 / z0 the level-0 right-hand side and result (precision T).
 template <typename T>
 bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream_t s) {
-  const int np = D.np;
   const int nlev = D.nlev;
   const double w = o.omega;
   if (nlev == 1) {
@@ -769,6 +825,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   // downward sweep
   for (int l = 0; l + 1 < nlev; ++l) {
     DevLevel& L = D.lev[l];
+    const int np = L.np;
     T* x = (T*)L.x;
     T* t = (T*)L.t;
     const T* b = bl[l];
@@ -784,16 +841,13 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
       if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, D.scal + S_FLAG,
                          unr_of<T>(L, 1)))
         return false;
-      if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), (const T*)L.r,
-                              (T*)D.lev[l + 1].b, s))
-        return false;
+      if (!transfer_restrict<T>(D, l, opL<T>(L), (const T*)L.r, (T*)D.lev[l + 1].b, s)) return false;
       // remember which buffer holds x
       L.x = x;
       L.t = t;
     } else {
       if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, (T*)nullptr, w, s)) return false;
-      if (!launch_restrict<T>(np, D.lev[l + 1].n, D.lev[l + 1].childptr, opL<T>(L), b, (T*)D.lev[l + 1].b, s))
-        return false;
+      if (!transfer_restrict<T>(D, l, opL<T>(L), b, (T*)D.lev[l + 1].b, s)) return false;
     }
   }
   // coarsest
@@ -805,10 +859,10 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   // upward sweep
   for (int l = nlev - 2; l >= 0; --l) {
     DevLevel& L = D.lev[l];
+    const int np = L.np;
     T* x = (T*)L.x;
     T* t = (T*)L.t;
-    if (!launch_prolong<T>(np, L.n, L.parent, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s))
-      return false;
+    if (!transfer_prolong<T>(D, l, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s)) return false;
     for (int k = 0; k < o.nu_post; ++k) {
       T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
       if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s,
@@ -925,8 +979,8 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
     return CDG_EINVAL;
   }
   const DevLevel& L = D.lev[level];
-  if ((int64_t)L.n * D.np > (int64_t)CDG_STATIC_SCRATCH) {
-    h->err = "cdg_smooth_static: level has " + std::to_string((int64_t)L.n * D.np) +
+  if ((int64_t)L.n * L.np > (int64_t)CDG_STATIC_SCRATCH) {
+    h->err = "cdg_smooth_static: level has " + std::to_string((int64_t)L.n * L.np) +
              " unknowns, more than the fixed scratch of " + std::to_string((int64_t)CDG_STATIC_SCRATCH);
     return CDG_EINVAL;
   }
@@ -950,8 +1004,8 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
     scratch = g_static_ptr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const bool ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, scratch, (double*)nullptr, h->opt.omega, s) &&
-                  launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)scratch, y,
+  const bool ok = launch_smooth_first<double>(L.np, L.n, L.Dinv, b, scratch, (double*)nullptr, h->opt.omega, s) &&
+                  launch_bsr<double>(3, L.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)scratch, y,
                                      h->opt.omega, nullptr, s,
                                      (((uintptr_t)x | (uintptr_t)y) & 15) == 0 ? D.scal + S_FLAG : nullptr);
   if (!ok) {
@@ -994,7 +1048,6 @@ void dev_release(cdg_handle* h) {
 // same order, so the choice changes the timing only, never a result.
 static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
   DeviceState& D = *h->dev;
-  if (D.np % 2 != 0) return CDG_OK;   // odd n_p: the scalar-load kernel has no variants
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1013,10 +1066,11 @@ static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
     }
     return best;
   };
-  const int np = D.np;
+  // odd n_p: the scalar-load kernel has no variants (levels keep the default)
   // level 0, FP64: the outer apply and residual
-  {
+  if (D.lev[0].np % 2 == 0) {
     DevLevel& L = D.lev[0];
+    const int np = L.np;
     const size_t nb = sizeof(double) * (size_t)D.ndofs;
     cudaMemsetAsync(D.p, 0, nb, s);
     cudaMemsetAsync(D.q, 0, nb, s);
@@ -1031,6 +1085,8 @@ static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
   // V-cycle levels in the V-cycle precision: residual and smoother sweep
   auto tune_level = [&](auto zero, DevLevel& L, int l) {
     using T = decltype(zero);
+    const int np = L.np;
+    if (np % 2 != 0) return;
     const int ti = sizeof(T) == 8 ? 0 : 1;
     const size_t nb = sizeof(T) * (size_t)L.n * np;
     T *x = (T*)L.x, *b = (T*)L.b, *bh = (T*)L.bh, *y = (T*)L.t;
@@ -1062,7 +1118,7 @@ int dev_tuning(const cdg_handle* h, int level, int32_t* out) {
   for (int k = 0; k < 10; ++k) out[k] = 0;
   const DeviceState& D = *h->dev;
   const DevLevel& L = D.lev[level];
-  const bool vec = D.np % 2 == 0;
+  const bool vec = L.np % 2 == 0;
   if (vec && level == 0) {
     out[0] = L.unr[0][0];
     out[1] = L.unr[0][1];
@@ -1128,7 +1184,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
     const std::vector<cdg::i64>& rc = H.seg_rows[D.nlev - 1];
     for (int m = 0; m <= D.nseg; ++m) {
       sd[m] = (long long)r0[m] * D.np;
-      cro[m] = (int)(rc[m] * D.np);
+      cro[m] = (int)(rc[m] * D.lev[D.nlev - 1].np);
       co[m] = (long long)H.seg_coarse[m];
     }
     for (int m = 0; m < D.nseg; ++m)
@@ -1220,15 +1276,15 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)b) & 15) == 0;
   double* flag = aligned ? D.scal + S_FLAG : nullptr;
   if (op <= 1) {
-    ok = launch_bsr<double>(op, D.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s, flag,
+    ok = launch_bsr<double>(op, L.np, L.n, L.rowptr, L.col, L.A, x, b, y, h->opt.omega, nullptr, s, flag,
                             unr_of<double>(L, op));
   } else if (op == 2) {
-    ok = launch_smooth_first<double>(D.np, L.n, L.Dinv, b, (double*)L.bh, (double*)nullptr, h->opt.omega, s) &&
-         launch_bsr<double>(3, D.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)L.bh, y, h->opt.omega,
+    ok = launch_smooth_first<double>(L.np, L.n, L.Dinv, b, (double*)L.bh, (double*)nullptr, h->opt.omega, s) &&
+         launch_bsr<double>(3, L.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)L.bh, y, h->opt.omega,
                             nullptr, s, flag, unr_of<double>(L, 3));
   }
-  else if (op == 3) ok = launch_restrict<double>(D.np, D.lev[level + 1].n, D.lev[level + 1].childptr, L.L, x, y, s);
-  else ok = launch_prolong<double>(D.np, L.n, L.parent, L.L, x, y, true, s);
+  else if (op == 3) ok = transfer_restrict<double>(D, level, L.L, x, y, s);
+  else ok = transfer_prolong<double>(D, level, L.L, x, y, true, s);
   if (!ok) {
     h->err = "unsupported n_p";
     return CDG_EINVAL;

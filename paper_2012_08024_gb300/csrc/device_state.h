@@ -17,6 +17,8 @@ enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, 
 
 struct DevLevel {
   int n = 0;
+  int np = 0;                // basis functions per element on this level
+  bool ptrans = false;       // level l -> l+1 lowers the degree on the same elements (truncation)
   int64_t nnzb = 0;
   int* rowptr = nullptr;
   int* col = nullptr;

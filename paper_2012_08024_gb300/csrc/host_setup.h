@@ -67,6 +67,7 @@ struct Options {
   std::vector<i64> enumeration;      // optional element enumeration for the natural switch
   int coarsen = 0;                   // 0 flux, 1 primal
   std::vector<double> kappa;         // optional per-element diffusion (input order)
+  int pmg = 0;                       // 1: degrees p, p-1, ..., 2 on the fine mesh before the p = 1 hierarchy
 };
 
 // ---------------------------------------------------------------- level-0 mesh
@@ -108,8 +109,12 @@ struct Hierarchy {
   Mesh0 mesh;
   Monomials mono;
   Rule vrule, frule;
-  int np = 0;
+  int np = 0;                     // basis functions per element on level 0
   std::vector<Level> lev;
+  // p-multigrid: the first n_plevels levels are degrees p, p-1, ..., 2 on the fine mesh
+  // (rediscretised; truncation transfers), then the degree-1 agglomeration hierarchy
+  int n_plevels = 0;
+  std::vector<int> np_l;          // basis functions per element, per level
   // tree numbering: order[l][final] = working id; pos[l][working] = final
   std::vector<std::vector<i64>> order, pos;
   // level data in tree order (what the device uses)
@@ -154,6 +159,12 @@ void build_level0(Hierarchy& H);
 void agglomerate(Hierarchy& H);
 void coarsen(Hierarchy& H);
 void finalize_tree_order(Hierarchy& H);
+// tree-order operator of level l with n_p = np, and (unless last) its block
+// inverses and the row-scaled smoother operator Ahat
+void tree_level(Hierarchy& H, int l, int np, bool last);
+// p-multigrid hierarchy: H holds level 0 at degree p (built), fine[q] the
+// rediscretised operators of degrees p-1, ..., 2, H1 the degree-1 hierarchy
+void merge_pmg(Hierarchy& H, std::vector<Hierarchy>& fine, Hierarchy& H1);
 void build_rhs_data(Hierarchy& H);
 
 // basis helpers

@@ -39,6 +39,7 @@ void concat_hierarchies(std::vector<Hierarchy>& subs, Hierarchy& B) {
   B.vrule = F.vrule;
   B.frule = F.frule;
   B.np = F.np;
+  B.np_l.assign(nlev, F.np);
   B.mesh.d = F.mesh.d;
   B.lev.assign(nlev, Level());
   B.A_t.assign(nlev, BSR());

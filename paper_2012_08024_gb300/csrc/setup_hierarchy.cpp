@@ -413,9 +413,77 @@ void coarsen(Hierarchy& H) {
 }
 
 // ------------------------------------------------------------------ tree order
+void tree_level(Hierarchy& H, int l, int np, bool last) {
+  const size_t nb2 = (size_t)np * np;
+  const Level& Lv = H.lev[l];
+  const BSR& A = Lv.A;
+  BSR& T = H.A_t[l];
+  const i64 n = Lv.n;
+  T.nrows = T.ncols = n;
+  T.br = T.bc = np;
+  T.rowptr.assign(n + 1, 0);
+  for (i64 k = 0; k < n; ++k) {
+    const i64 r = H.order[l][k];
+    T.rowptr[k + 1] = T.rowptr[k] + (A.rowptr[r + 1] - A.rowptr[r]);
+  }
+  T.col.resize(T.rowptr[n]);
+  T.val.resize((size_t)T.rowptr[n] * nb2);
+  bool notspd = false;
+  if (!last) H.Dinv_t[l].assign((size_t)n * nb2, 0.0);
+#pragma omp parallel for schedule(static)
+  for (i64 k = 0; k < n; ++k) {
+    const i64 r = H.order[l][k];
+    std::vector<std::pair<i32, i64>> cb;
+    for (i64 b = A.rowptr[r]; b < A.rowptr[r + 1]; ++b) cb.push_back({(i32)H.pos[l][A.col[b]], b});
+    std::sort(cb.begin(), cb.end());
+    for (size_t t = 0; t < cb.size(); ++t) {
+      T.col[T.rowptr[k] + t] = cb[t].first;
+      std::memcpy(T.block(T.rowptr[k] + t), A.block(cb[t].second), nb2 * sizeof(double));
+      if (cb[t].first == k && !last) {
+        // flux-coarsened operators need not be definite (observed on 3D meshes):
+        // fall back to a pivoted inverse when the Cholesky factorisation fails
+        if (!spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]) &&
+            !lu_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]))
+          notspd = true;
+      }
+    }
+  }
+  if (notspd) throw std::runtime_error("singular diagonal block on level " + std::to_string(l));
+  if (!last) {
+    // row-scaled off-diagonal operator Ahat = D^{-1} (A - D) used by the smoother:
+    // x + omega D^{-1}(b - A x) = x + omega (D^{-1} b - x - Ahat x)
+    BSR& S = H.Ahat_t[l];
+    S.nrows = S.ncols = n;
+    S.br = S.bc = np;
+    S.rowptr.assign(n + 1, 0);
+    for (i64 k = 0; k < n; ++k) S.rowptr[k + 1] = S.rowptr[k] + (T.rowptr[k + 1] - T.rowptr[k] - 1);
+    S.col.resize(S.rowptr[n]);
+    S.val.assign((size_t)S.rowptr[n] * nb2, 0.0);
+#pragma omp parallel for schedule(static)
+    for (i64 k = 0; k < n; ++k) {
+      i64 o = S.rowptr[k];
+      const double* Di = &H.Dinv_t[l][k * nb2];
+      for (i64 b = T.rowptr[k]; b < T.rowptr[k + 1]; ++b) {
+        if (T.col[b] == k) continue;
+        S.col[o] = T.col[b];
+        const double* Ab = T.block(b);
+        double* Sb = S.block(o);
+        for (int i = 0; i < np; ++i)
+          for (int j = 0; j < np; ++j) {
+            double acc = 0.0;
+            for (int m = 0; m < np; ++m) acc += Di[i * np + m] * Ab[m * np + j];
+            Sb[i * np + j] = acc;
+          }
+        ++o;
+      }
+    }
+  }
+}
+
 void finalize_tree_order(Hierarchy& H) {
   const int nlev = (int)H.lev.size();
   const int np = H.np;
+  H.np_l.assign(nlev, np);
   const size_t nb2 = (size_t)np * np;
   H.A_t.assign(nlev, BSR());
   H.Dinv_t.assign(nlev, {});
@@ -425,68 +493,8 @@ void finalize_tree_order(Hierarchy& H) {
   H.childptr_t.assign(nlev, {});
   for (int l = 0; l < nlev; ++l) {
     const Level& Lv = H.lev[l];
-    const BSR& A = Lv.A;
-    BSR& T = H.A_t[l];
     const i64 n = Lv.n;
-    T.nrows = T.ncols = n;
-    T.br = T.bc = np;
-    T.rowptr.assign(n + 1, 0);
-    for (i64 k = 0; k < n; ++k) {
-      const i64 r = H.order[l][k];
-      T.rowptr[k + 1] = T.rowptr[k] + (A.rowptr[r + 1] - A.rowptr[r]);
-    }
-    T.col.resize(T.rowptr[n]);
-    T.val.resize((size_t)T.rowptr[n] * nb2);
-    bool notspd = false;
-    if (l + 1 < nlev) H.Dinv_t[l].assign((size_t)n * nb2, 0.0);
-#pragma omp parallel for schedule(static)
-    for (i64 k = 0; k < n; ++k) {
-      const i64 r = H.order[l][k];
-      std::vector<std::pair<i32, i64>> cb;
-      for (i64 b = A.rowptr[r]; b < A.rowptr[r + 1]; ++b) cb.push_back({(i32)H.pos[l][A.col[b]], b});
-      std::sort(cb.begin(), cb.end());
-      for (size_t t = 0; t < cb.size(); ++t) {
-        T.col[T.rowptr[k] + t] = cb[t].first;
-        std::memcpy(T.block(T.rowptr[k] + t), A.block(cb[t].second), nb2 * sizeof(double));
-        if (cb[t].first == k && l + 1 < nlev) {
-          // flux-coarsened operators need not be definite (observed on 3D meshes):
-          // fall back to a pivoted inverse when the Cholesky factorisation fails
-          if (!spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]) &&
-              !lu_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]))
-            notspd = true;
-        }
-      }
-    }
-    if (notspd) throw std::runtime_error("singular diagonal block on level " + std::to_string(l));
-    if (l + 1 < nlev) {
-      // row-scaled off-diagonal operator Ahat = D^{-1} (A - D) used by the smoother:
-      // x + omega D^{-1}(b - A x) = x + omega (D^{-1} b - x - Ahat x)
-      BSR& S = H.Ahat_t[l];
-      S.nrows = S.ncols = n;
-      S.br = S.bc = np;
-      S.rowptr.assign(n + 1, 0);
-      for (i64 k = 0; k < n; ++k) S.rowptr[k + 1] = S.rowptr[k] + (T.rowptr[k + 1] - T.rowptr[k] - 1);
-      S.col.resize(S.rowptr[n]);
-      S.val.assign((size_t)S.rowptr[n] * nb2, 0.0);
-#pragma omp parallel for schedule(static)
-      for (i64 k = 0; k < n; ++k) {
-        i64 o = S.rowptr[k];
-        const double* Di = &H.Dinv_t[l][k * nb2];
-        for (i64 b = T.rowptr[k]; b < T.rowptr[k + 1]; ++b) {
-          if (T.col[b] == k) continue;
-          S.col[o] = T.col[b];
-          const double* Ab = T.block(b);
-          double* Sb = S.block(o);
-          for (int i = 0; i < np; ++i)
-            for (int j = 0; j < np; ++j) {
-              double acc = 0.0;
-              for (int m = 0; m < np; ++m) acc += Di[i * np + m] * Ab[m * np + j];
-              Sb[i * np + j] = acc;
-            }
-          ++o;
-        }
-      }
-    }
+    tree_level(H, l, np, l + 1 == nlev);
     if (l + 1 < nlev) {
       H.L_t[l].resize((size_t)n * nb2);
       H.parent_t[l].resize(n);
@@ -519,6 +527,73 @@ void finalize_tree_order(Hierarchy& H) {
   if (!spd_inverse((int)nc, dense.data(), H.coarse_inv.data()) &&
       !lu_inverse((int)nc, dense.data(), H.coarse_inv.data()))
     throw std::runtime_error("singular coarsest operator");
+  H.seg_coarse = {0, (i64)H.coarse_inv.size()};
+}
+
+// p-multigrid hierarchy (Section 4.4; reading R17).  Levels 0..P-1 hold the
+// CDG operator rediscretised at degrees p, p-1, ..., 2 on the fine mesh (every
+// element its own coarse element; the transfer between consecutive degrees is
+// the truncation [I; 0] of the nested orthonormal bases, applied on the device
+// without stored blocks), followed by the whole degree-1 hierarchy H1.  On
+// entry H.lev[0] holds degree p and fine[i].lev[0] degree p-1-i (working order).
+void merge_pmg(Hierarchy& H, std::vector<Hierarchy>& fine, Hierarchy& H1) {
+  const int P = 1 + (int)fine.size();
+  const int nh = (int)H1.lev.size();
+  const int nlev = P + nh;
+  const i64 ne = H.mesh.ne;
+  std::vector<Level> lev;
+  lev.reserve(nlev);
+  lev.push_back(std::move(H.lev[0]));
+  H.np_l.assign(1, H.np);
+  for (Hierarchy& F : fine) {
+    lev.push_back(std::move(F.lev[0]));
+    H.np_l.push_back(F.np);
+  }
+  for (Level& L : H1.lev) {
+    lev.push_back(std::move(L));
+    H.np_l.push_back(H1.np);
+  }
+  H.lev = std::move(lev);
+  H.n_plevels = P;
+  for (int l = 0; l < P; ++l) {
+    Level& L = H.lev[l];
+    L.n = ne;
+    L.parent.resize(ne);
+    for (i64 K = 0; K < ne; ++K) L.parent[K] = K;
+  }
+  H.order.assign(P, H1.order[0]);
+  H.pos.assign(P, H1.pos[0]);
+  for (int h = 0; h < nh; ++h) {
+    H.order.push_back(H1.order[h]);
+    H.pos.push_back(H1.pos[h]);
+  }
+  H.A_t.assign(nlev, BSR());
+  H.Dinv_t.assign(nlev, {});
+  H.Ahat_t.assign(nlev, BSR());
+  H.L_t.assign(nlev, {});
+  H.parent_t.assign(nlev, {});
+  H.childptr_t.assign(nlev, {});
+  std::vector<i32> ident(ne), identp(ne + 1);
+  for (i64 K = 0; K < ne; ++K) ident[K] = (i32)K;
+  for (i64 K = 0; K <= ne; ++K) identp[K] = (i32)K;
+  for (int l = 0; l < P; ++l) {
+    tree_level(H, l, H.np_l[l], false);
+    H.parent_t[l] = ident;
+    H.childptr_t[l + 1] = identp;
+  }
+  for (int h = 0; h < nh; ++h) {
+    const int l = P + h;
+    H.A_t[l] = std::move(H1.A_t[h]);
+    H.Dinv_t[l] = std::move(H1.Dinv_t[h]);
+    H.Ahat_t[l] = std::move(H1.Ahat_t[h]);
+    H.L_t[l] = std::move(H1.L_t[h]);
+    H.parent_t[l] = std::move(H1.parent_t[h]);
+    if (h > 0) H.childptr_t[l] = std::move(H1.childptr_t[h]);
+  }
+  H.seg_rows.assign(nlev, {});
+  for (int l = 0; l < nlev; ++l) H.seg_rows[l] = {0, H.lev[l].n};
+  H.seg_bface = {0, (i64)H.mesh.bf_K.size()};
+  H.coarse_inv = std::move(H1.coarse_inv);
   H.seg_coarse = {0, (i64)H.coarse_inv.size()};
 }
 

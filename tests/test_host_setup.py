@@ -40,6 +40,10 @@ CASES = [
     ("tri_natural", lambda: jittered_square(5), dict(p=1, max_levels=3, switch_kind=1)),
     ("tri_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3,
                                                   kappa=np.exp(np.random.default_rng(1).standard_normal(50)))),
+    ("tri_p3_pmg", lambda: jittered_square(8, neumann_axes=(1,)), dict(p=3, max_levels=3, pmg=True)),
+    ("tet_p2_pmg", lambda: kuhn_cube(2), dict(p=2, max_levels=3, pmg=True)),
+    ("tri_p2_pmg_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3, pmg=True,
+                                                         kappa=np.exp(np.random.default_rng(2).standard_normal(50)))),
 ]
 
 
@@ -50,15 +54,16 @@ def test_library_setup_matches_oracle(name, mk, kw):
     S = Solver(mesh, **kw)
     okw = dict(p=kw["p"], switch_kind=kw.get("switch_kind", 0), kappa=kw.get("kappa"))
     L0 = Level0(mesh, **okw)
-    H = MGHierarchy(L0, max_levels=kw["max_levels"], seed=kw.get("seed", 0))
+    H = MGHierarchy(L0, max_levels=kw["max_levels"], seed=kw.get("seed", 0), pmg=kw.get("pmg", False))
     assert S.n_levels == H.n_levels
-    order = H.agg.tree_order()
-    npb = L0.np_
+    assert S.info["np_l"] == H.nps and S.info["n_plevels"] == H.n_plevels
+    order = H.tree_order()
     for l in range(H.n_levels - 1):
-        assert list(S.export_agglomeration(l)) == H.agg.parent[l]
+        assert list(S.export_agglomeration(l)) == list(H.parent[l])
     for l in range(H.n_levels):
+        npb = H.nps[l]
         ex = S.export_level(l)
-        assert list(ex["perm"]) == order[l]
+        assert list(ex["perm"]) == list(order[l])
         n = len(order[l])
         P = np.zeros((n * npb, n * npb))
         for k, w in enumerate(order[l]):
@@ -70,7 +75,7 @@ def test_library_setup_matches_oracle(name, mk, kw):
             Lor = np.array([H.Lblk[l][w] for w in order[l]])
             assert np.abs(ex["L"] - Lor).max() <= 1e-12
             pos = {w: k for k, w in enumerate(order[l + 1])}
-            assert list(ex["parent"]) == [pos[H.agg.parent[l][w]] for w in order[l]]
+            assert list(ex["parent"]) == [pos[H.parent[l][w]] for w in order[l]]
     xq, xbq, btag = S.quadrature_points()
     assert np.abs(xq - L0.all_volume_points()).max() < 1e-14
     assert np.abs(xbq - L0.all_boundary_points()).max() < 1e-14
