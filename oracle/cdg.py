@@ -42,8 +42,11 @@ from .quadrature import simplex_rule, map_simplex
 
 class Level0:
     def __init__(self, mesh, p: int, gamma: float = 1e4, switch_kind: int = 0,
-                 face_switch=None, enumeration=None, kappa=None):
+                 face_switch=None, enumeration=None, kappa=None, beta: float = 0.0, velocity=None):
         self.topo = t = Topology(mesh, switch_kind, face_switch, enumeration)
+        # convection beta v . grad u (Section 5, convection-diffusion; R18: upwind DG)
+        self.beta = float(beta)
+        self.vel = np.zeros(t.d) if velocity is None else np.asarray(velocity, dtype=np.float64)[:t.d]
         self.p = p
         self.d = d = t.d
         self.bases = [Basis([t.simplex(K)], p) for K in range(t.ne)]
@@ -61,6 +64,7 @@ class Level0:
         other.bases = [Basis([self.topo.simplex(K)], q) for K in range(self.topo.ne)]
         other.np_ = len(other.bases[0].exps)
         other.C_D, other.kappa = self.C_D, self.kappa
+        other.beta, other.vel = self.beta, self.vel
         other.vrule = simplex_rule(self.d, 2 * q)
         other.frule = simplex_rule(self.d - 1, 2 * q)
         return other
@@ -140,6 +144,45 @@ class Level0:
             if tag == 0:
                 K, blk = self.dirichlet_block(bf)
                 add(K, K, blk)
+        if self.beta != 0.0:
+            for (i, j), m in self.convection_blocks().items():
+                add(i, j, m)
+        return B
+
+    def convection_blocks(self):
+        """R18: the convection term beta v . grad u of -div(kappa grad u) +
+        beta v . grad u = f in upwind DG form (constant v, so div v = 0): on
+        each element  -int_K u beta v.grad w  +  int_{dK} beta (v.n) u-hat w,
+        u-hat the upwind trace (the element the flow leaves, v.n > 0 side), on
+        the boundary u-hat = u_K at outflow and on Neumann faces, g_D at
+        Dirichlet inflow (a right-hand-side term)."""
+        t = self.topo
+        bv = self.beta * self.vel
+        B: dict[tuple[int, int], np.ndarray] = {}
+
+        def add(i, j, m):
+            B[(i, j)] = B[(i, j)] + m if (i, j) in B else m.copy()
+        for K in range(t.ne):
+            x, w = self.volume_points(K)
+            ph = self.bases[K].eval(x)
+            vg = self.bases[K].grad(x) @ bv                 # v . grad phi_i at the points
+            add(K, K, -(vg * w[:, None]).T @ ph)
+        for f, (K1, K2, _, _) in enumerate(t.interior):
+            vn = float(bv @ t.if_n[f])                       # out of K1
+            x, w = self.interior_face_points(f)
+            p1, p2 = self.bases[K1].eval(x), self.bases[K2].eval(x)
+            if vn > 0:      # flow leaves K1: u-hat = u_K1
+                add(K1, K1, vn * (p1 * w[:, None]).T @ p1)
+                add(K2, K1, -vn * (p2 * w[:, None]).T @ p1)
+            elif vn < 0:    # flow leaves K2: u-hat = u_K2
+                add(K1, K2, vn * (p1 * w[:, None]).T @ p2)
+                add(K2, K2, -vn * (p2 * w[:, None]).T @ p2)
+        for bf, (K, l, tag) in enumerate(t.boundary):
+            vn = float(bv @ t.bf_n[bf])
+            if vn > 0 or (tag == 1 and vn != 0):
+                x, w = self.boundary_face_points(bf)
+                ph = self.bases[K].eval(x)
+                add(K, K, vn * (ph * w[:, None]).T @ ph)
         return B
 
     def matrix(self):
@@ -222,6 +265,9 @@ class Level0:
             if tag == 0 and gD_q is not None:
                 dn = self.bases[K].grad(x) @ t.bf_n[bf]
                 b[K] += self.kappa[K] * ((-dn + self.C_D * ph) * (w * gD_q[bf])[:, None]).sum(axis=0)
+                vn = self.beta * float(self.vel @ t.bf_n[bf])
+                if vn < 0:      # R18: Dirichlet inflow, u-hat = g_D
+                    b[K] += -vn * (ph * (w * gD_q[bf])[:, None]).sum(axis=0)
             if tag == 1 and gN_q is not None:
                 b[K] += (ph * (w * gN_q[bf])[:, None]).sum(axis=0)
         return b.ravel()
