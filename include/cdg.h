@@ -101,6 +101,11 @@ typedef struct {
                                the fastest, and the first cdg_solve_multi does the same for the
                                right-hand-side tile width and block rows per CTA; 0: fixed
                                defaults.  Results are bit-identical either way. */
+  double beta;              /* convection-diffusion (Section 5): solve -div(kappa grad u) +
+                               beta v . grad u = f, convection in upwind DG form, constant v;
+                               A_0 is then non-symmetric: needs krylov = 1, nrhs = 0, no
+                               batched handle, no adjoint.  Default 0 (Poisson). */
+  double velocity[3];       /* v (first dim entries used) */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16

@@ -39,7 +39,8 @@ class cdg_options(C.Structure):
                 ("precision", C.c_int32), ("switch_kind", C.c_int32), ("face_switch", C.c_void_p),
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
-                ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32)]
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32),
+                ("beta", C.c_double), ("velocity", C.c_double * 3)]
 
 
 class cdg_info(C.Structure):
@@ -137,7 +138,8 @@ class Solver:
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
-                 krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False):
+                 krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False,
+                 beta: float = 0.0, velocity=(0.0, 0.0, 0.0)):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -157,6 +159,10 @@ class Solver:
         o.nrhs = nrhs
         o.krylov, o.restart, o.autotune = KRYLOV[krylov], restart, int(autotune)
         o.pmg = int(pmg)
+        o.beta = beta
+        vel = list(velocity) + [0.0] * (3 - len(velocity))
+        for c in range(3):
+            o.velocity[c] = float(vel[c])
         arrs = {}
         if face_switch is not None:
             arrs["fs"] = np.ascontiguousarray(face_switch, dtype=np.int8)

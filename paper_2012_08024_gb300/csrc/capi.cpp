@@ -43,6 +43,13 @@ static int check_options(const cdg_options* opt) {
     return fail(nullptr, CDG_EINVAL, "p-multigrid: max_levels + p - 1 must be at most 16");
   if (opt->pmg && opt->p > 1 && opt->nrhs)
     return fail(nullptr, CDG_EINVAL, "p-multigrid is not available with nrhs (cdg_solve_multi)");
+  if (!std::isfinite(opt->beta) || !std::isfinite(opt->velocity[0]) || !std::isfinite(opt->velocity[1]) ||
+      !std::isfinite(opt->velocity[2]))
+    return fail(nullptr, CDG_EINVAL, "beta and velocity must be finite");
+  if (opt->beta != 0.0 && opt->krylov != 1)
+    return fail(nullptr, CDG_EINVAL, "convection makes A_0 non-symmetric: use GMRES (krylov = 1)");
+  if (opt->beta != 0.0 && opt->nrhs)
+    return fail(nullptr, CDG_EINVAL, "convection is not available with nrhs (cdg_solve_multi runs CG)");
   return CDG_OK;
 }
 
@@ -61,6 +68,8 @@ static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arr
   cdg::Options& o = H.opt;
   o.p = opt->p;
   o.pmg = opt->pmg;
+  o.beta = opt->beta;
+  for (int c = 0; c < 3; ++c) o.vel[c] = opt->velocity[c];
   o.gamma = opt->gamma;
   o.nu_pre = opt->nu_pre;
   o.nu_post = opt->nu_post;
@@ -238,6 +247,7 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
     return fail(nullptr, CDG_EINVAL, "per-element arrays and nrhs are not supported for batched handles");
   if (opt->krylov != 0) return fail(nullptr, CDG_EINVAL, "batched handles solve with CG (krylov = 0)");
   if (opt->pmg != 0) return fail(nullptr, CDG_EINVAL, "p-multigrid is not available for batched handles");
+  if (opt->beta != 0.0) return fail(nullptr, CDG_EINVAL, "convection is not available for batched handles");
   int rc = check_options(opt);
   for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
   if (rc != CDG_OK) return rc;
@@ -458,6 +468,7 @@ int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
 int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,
                       void* stream) {
   // A_0 is symmetric: A^T lambda = dL/du is the same solve as A_0 u = b
+  if (h && h->opt.beta != 0.0) return fail(h, CDG_EINVAL, "no adjoint with convection (A_0 is not symmetric)");
   return cdg_solve_b(h, dLdu, lambda, 0, res_hist, iters, stream);
 }
 
@@ -469,6 +480,7 @@ int cdg_rhs_adjoint(cdg_handle* h, const double* lambda, double* dLdf_q, void* s
 int cdg_kappa_gradient(cdg_handle* h, const double* lambda, const double* u, const double* gD_q, double* dLdkappa,
                        void* stream) {
   if (!h || !lambda || !u || !dLdkappa) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  if (h->opt.beta != 0.0) return fail(h, CDG_EINVAL, "no adjoint with convection (A_0 is not symmetric)");
   return dev_adjoint(h, 1, lambda, u, gD_q, dLdkappa, stream);
 }
 

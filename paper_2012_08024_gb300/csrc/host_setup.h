@@ -68,6 +68,8 @@ struct Options {
   int coarsen = 0;                   // 0 flux, 1 primal
   std::vector<double> kappa;         // optional per-element diffusion (input order)
   int pmg = 0;                       // 1: degrees p, p-1, ..., 2 on the fine mesh before the p = 1 hierarchy
+  double beta = 0.0;                 // convection beta v . grad u (upwind DG, constant v)
+  double vel[3] = {0.0, 0.0, 0.0};
 };
 
 // ---------------------------------------------------------------- level-0 mesh

@@ -46,6 +46,111 @@ static void vol_point(const Mesh0& m, i64 K, const Rule& r, int q, double* x, do
 
 static inline double kap(const Options& o, i64 K) { return o.kappa.empty() ? 1.0 : o.kappa[K]; }
 
+// R18: the convection term beta v . grad u of -div(kappa grad u) + beta v . grad u
+// = f in upwind DG form (constant v): on each element -int_K u beta v.grad w plus
+// int_{dK} beta (v.n) u-hat w with u-hat the trace of the element the flow
+// leaves; on the boundary u-hat = u_K at outflow and on Neumann faces, and g_D
+// at Dirichlet inflow, which becomes a right-hand-side term (added to the
+// boundary data that multiplies g_D).  Added to A_0 after its assembly.
+static void add_convection(Hierarchy& H) {
+  const Mesh0& m = H.mesh;
+  const int d = m.d, np = H.np;
+  const i64 ne = m.ne, nif = (i64)m.if_K1.size(), nbf = (i64)m.bf_K.size();
+  const BasisSet& B = H.lev[0].basis;
+  BSR& A = H.lev[0].A;
+  const size_t nb2 = (size_t)np * np;
+  const int nq = H.vrule.n(), nfq = H.frule.n();
+  double bv[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < d; ++c) bv[c] = H.opt.beta * H.opt.vel[c];
+  auto block = [&](i64 K, i64 J) {
+    const auto first = A.col.begin() + A.rowptr[K], last = A.col.begin() + A.rowptr[K + 1];
+    const auto it = std::lower_bound(first, last, (i32)J);
+    if (it == last || *it != (i32)J) throw std::logic_error("convection block outside the pattern of A_0");
+    return A.block(A.rowptr[K] + (it - first));
+  };
+  // volume: row K only
+#pragma omp parallel for schedule(static)
+  for (i64 K = 0; K < ne; ++K) {
+    double* blk = block(K, K);
+    double x[3], w, ph[64], g[64 * 3], vg[64];
+    for (int q = 0; q < nq; ++q) {
+      vol_point(m, K, H.vrule, q, x, w);
+      basis_eval(H, B, K, x, ph);
+      basis_grad(H, B, K, x, g);
+      for (int i = 0; i < np; ++i) {
+        double s = 0.0;
+        for (int c = 0; c < d; ++c) s += bv[c] * g[i * d + c];
+        vg[i] = s;
+      }
+      for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) blk[i * np + j] -= w * vg[i] * ph[j];
+    }
+  }
+  // interior faces: two blocks each (rows K1 and K2), computed in parallel, added in face order
+  std::vector<double> Fc((size_t)nif * 2 * nb2, 0.0);
+#pragma omp parallel for schedule(static)
+  for (i64 f = 0; f < nif; ++f) {
+    const i64 K1 = m.if_K1[f], K2 = m.if_K2[f];
+    double vn = 0.0;
+    for (int c = 0; c < d; ++c) vn += bv[c] * m.if_n[f * d + c];
+    if (vn == 0.0) continue;
+    const i64 up = vn > 0 ? K1 : K2;   // the element the flow leaves
+    double* b1 = &Fc[(f * 2 + 0) * nb2];
+    double* b2 = &Fc[(f * 2 + 1) * nb2];
+    for (int q = 0; q < nfq; ++q) {
+      double x[3], w, p1[64], pu[64], p2[64];
+      face_point(d, &m.if_xv[f * d * d], H.frule, q, m.if_meas[f], x, w);
+      basis_eval(H, B, K1, x, p1);
+      basis_eval(H, B, K2, x, p2);
+      basis_eval(H, B, up, x, pu);
+      for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) {
+          b1[i * np + j] += vn * w * p1[i] * pu[j];    // row K1: + vn int u-hat w_1
+          b2[i * np + j] -= vn * w * p2[i] * pu[j];    // row K2: - vn int u-hat w_2
+        }
+    }
+  }
+  for (i64 f = 0; f < nif; ++f) {
+    double vn = 0.0;
+    for (int c = 0; c < d; ++c) vn += bv[c] * m.if_n[f * d + c];
+    if (vn == 0.0) continue;
+    const i64 K1 = m.if_K1[f], K2 = m.if_K2[f], up = vn > 0 ? K1 : K2;
+    double* a1 = block(K1, up);
+    double* a2 = block(K2, up);
+    for (size_t t = 0; t < nb2; ++t) {
+      a1[t] += Fc[(f * 2 + 0) * nb2 + t];
+      a2[t] += Fc[(f * 2 + 1) * nb2 + t];
+    }
+  }
+  // boundary faces: outflow and Neumann faces keep u_K (block), Dirichlet inflow moves g_D
+  // to the right-hand side
+  std::vector<double> Bc((size_t)nbf * nb2, 0.0);
+#pragma omp parallel for schedule(static)
+  for (i64 bfi = 0; bfi < nbf; ++bfi) {
+    const i64 K = m.bf_K[bfi];
+    double vn = 0.0;
+    for (int c = 0; c < d; ++c) vn += bv[c] * m.bf_n[bfi * d + c];
+    if (vn == 0.0) continue;
+    const bool keep = vn > 0 || m.bf_tag[bfi] == 1;
+    double* rb = &H.rhs_bD[(size_t)bfi * nfq * np];
+    for (int q = 0; q < nfq; ++q) {
+      double x[3], w, ph[64];
+      face_point(d, &m.bf_xv[bfi * d * d], H.frule, q, m.bf_meas[bfi], x, w);
+      basis_eval(H, B, K, x, ph);
+      if (keep) {
+        for (int i = 0; i < np; ++i)
+          for (int j = 0; j < np; ++j) Bc[bfi * nb2 + i * np + j] += vn * w * ph[i] * ph[j];
+      } else {
+        for (int i = 0; i < np; ++i) rb[q * np + i] += -vn * w * ph[i];
+      }
+    }
+  }
+  for (i64 bfi = 0; bfi < nbf; ++bfi) {
+    double* a = block(m.bf_K[bfi], m.bf_K[bfi]);
+    for (size_t t = 0; t < nb2; ++t) a[t] += Bc[bfi * nb2 + t];
+  }
+}
+
 void build_level0(Hierarchy& H) {
   Mesh0& m = H.mesh;
   const int d = m.d, np = H.np, nvk = d + 1;
@@ -346,6 +451,7 @@ void build_level0(Hierarchy& H) {
       }
     }
   }
+  if (H.opt.beta != 0.0) add_convection(H);
 }
 
 }  // namespace cdg

@@ -442,7 +442,9 @@ void tree_level(Hierarchy& H, int l, int np, bool last) {
       if (cb[t].first == k && !last) {
         // flux-coarsened operators need not be definite (observed on 3D meshes):
         // fall back to a pivoted inverse when the Cholesky factorisation fails
-        if (!spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]) &&
+        // (a non-symmetric operator, with convection, always takes the pivoted inverse)
+        const bool sym = H.opt.beta == 0.0;
+        if (!(sym && spd_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2])) &&
             !lu_inverse(np, A.block(cb[t].second), &H.Dinv_t[l][k * nb2]))
           notspd = true;
       }
@@ -524,7 +526,7 @@ void finalize_tree_order(Hierarchy& H) {
         for (int j = 0; j < np; ++j)
           dense[(size_t)(k * np + i) * nc + T.col[b] * np + j] = T.block(b)[i * np + j];
   H.coarse_inv.assign((size_t)nc * nc, 0.0);
-  if (!spd_inverse((int)nc, dense.data(), H.coarse_inv.data()) &&
+  if (!(H.opt.beta == 0.0 && spd_inverse((int)nc, dense.data(), H.coarse_inv.data())) &&
       !lu_inverse((int)nc, dense.data(), H.coarse_inv.data()))
     throw std::runtime_error("singular coarsest operator");
   H.seg_coarse = {0, (i64)H.coarse_inv.size()};

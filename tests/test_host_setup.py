@@ -44,6 +44,12 @@ CASES = [
     ("tet_p2_pmg", lambda: kuhn_cube(2), dict(p=2, max_levels=3, pmg=True)),
     ("tri_p2_pmg_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3, pmg=True,
                                                          kappa=np.exp(np.random.default_rng(2).standard_normal(50)))),
+    ("tri_p2_convection", lambda: jittered_square(6, neumann_axes=(0,)),
+     dict(p=2, max_levels=3, beta=10.0, velocity=(1.0, 0.3), krylov="gmres")),
+    ("tet_p1_convection", lambda: kuhn_cube(2), dict(p=1, max_levels=3, beta=3.0, velocity=(0.2, -1.0, 0.5),
+                                                     krylov="gmres")),
+    ("tri_p3_pmg_convection", lambda: jittered_square(6), dict(p=3, max_levels=3, pmg=True, beta=50.0,
+                                                               velocity=(1.0, 0.0), krylov="gmres")),
 ]
 
 
@@ -52,7 +58,8 @@ def test_library_setup_matches_oracle(name, mk, kw):
     from paper_2012_08024_gb300 import Solver
     mesh = mk()
     S = Solver(mesh, **kw)
-    okw = dict(p=kw["p"], switch_kind=kw.get("switch_kind", 0), kappa=kw.get("kappa"))
+    okw = dict(p=kw["p"], switch_kind=kw.get("switch_kind", 0), kappa=kw.get("kappa"),
+               beta=kw.get("beta", 0.0), velocity=kw.get("velocity"))
     L0 = Level0(mesh, **okw)
     H = MGHierarchy(L0, max_levels=kw["max_levels"], seed=kw.get("seed", 0), pmg=kw.get("pmg", False))
     assert S.n_levels == H.n_levels
@@ -110,6 +117,15 @@ def test_errors_are_reported():
     with pytest.raises(CdgError) as e:
         Solver(m, p=0)
     assert e.value.code == 1
+
+
+def test_convection_options_are_checked():
+    from paper_2012_08024_gb300 import CdgError, Solver
+    m = jittered_square(4)
+    for kw in (dict(beta=1.0), dict(beta=1.0, krylov="gmres", nrhs=4), dict(beta=float("nan"), krylov="gmres")):
+        with pytest.raises(CdgError) as e:
+            Solver(m, p=1, velocity=(1.0, 0.0), **kw)
+        assert e.value.code == 1
 
 
 def test_gmres_options_and_device_bytes():
