@@ -168,16 +168,29 @@ def _time(fn, stream, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
-def run_extras(pkg, dev, stream, barrier):
+def run_extras(pkg, dev, stream, barrier, only=None):
     """The other workloads of the solve phase, each timed after one warm-up:
     64 meshes of 500-20000 triangles in one batched handle (p = 2) against the
     same meshes solved one after another; one 158 x 158 x 2 triangle mesh
     (p = 3) with 256 right-hand sides (sine combinations; FP32 and BF16 V-cycle blocks)
     against 256 single solves estimated from 8; the differentiable 24^3 x 6
-    tetrahedra workload (p = 2, smoothed log-normal kappa): forward + adjoint."""
+    tetrahedra workload (p = 2, smoothed log-normal kappa): forward + adjoint.
+    only: one of "batched", "multi_rhs", "adjoint" (None = all)."""
+    out = {}
+    if only in (None, "batched"):
+        out.update(extra_batched(pkg, dev, stream))
+    if only in (None, "multi_rhs"):
+        out.update(extra_multi_rhs(pkg, dev, stream))
+    if only in ("multi_rhs_bf16", "multi_rhs_bf16_cuda_cores"):   # one variant, no single solves
+        out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))
+    if only in (None, "adjoint"):
+        out.update(extra_adjoint(pkg, dev, stream))
+    return out
+
+
+def extra_batched(pkg, dev, stream):
     import torch
-    from synthetic import (batched_squares, face_neighbors, jittered_square, kuhn_cube, sin_source,
-                           sine_combination_sources, smoothed_lognormal_kappa)
+    from synthetic import batched_squares, sin_source
     out = {}
     # ---- batched meshes
     meshes = batched_squares(64, 500, 20000, seed=1)
@@ -199,6 +212,13 @@ def run_extras(pkg, dev, stream, barrier):
                                 "rc": rc, "launches_per_solve": nl, "sequential_ms": seq,
                                 "speedup_vs_sequential": seq / ms}
     del B
+    return out
+
+
+def extra_multi_rhs(pkg, dev, stream, variants=("fp32", "bf16", "bf16_cuda_cores"), singles=True):
+    import torch
+    from synthetic import jittered_square, sine_combination_sources
+    out = {}
     # ---- many right-hand sides on one mesh
     mesh = jittered_square(158)
     R = 256
@@ -206,20 +226,32 @@ def run_extras(pkg, dev, stream, barrier):
     xq = S1.quadrature_points()[0]
     fq = torch.tensor(sine_combination_sources(xq, R, mmax=8, seed0=0), device=dev)
     single = []
-    for r in range(8):
+    for r in range(8 if singles else 0):
         t, _ = _time(lambda: S1.solve(fq[r].contiguous()), stream, 1)
         single.append(t)
     del S1
-    for prec in ("fp32", "bf16"):
-        S = pkg.Solver(mesh, p=3, max_levels=5, nu_pre=2, nu_post=2, precision=prec, nrhs=R).bind(dev)
-        ms, (u, hists, its, rc) = _time(lambda: S.solve_multi(fq), stream, 2)
-        out["multi_rhs_256_" + prec] = {
+    # BF16 blocks: smoother sweeps on tcgen05 tensor cores (default) and on CUDA cores
+    for prec, tc, name in (("fp32", False, "fp32"), ("bf16", True, "bf16"), ("bf16", False, "bf16_cuda_cores")):
+        if name not in variants:
+            continue
+        S = pkg.Solver(mesh, p=3, max_levels=5, nu_pre=2, nu_post=2, precision=prec, nrhs=R,
+                       tensor_cores=tc).bind(dev)
+        ms, (u, hists, its, rc) = _time(lambda: S.solve_multi(fq), stream, 2 if singles else 1)
+        out["multi_rhs_256_" + name] = {
             "value": R * S.info["n_dofs"] / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms,
             "dofs_per_rhs": S.info["n_dofs"], "nrhs": R, "vcycle_blocks": prec,
+            "smoother_sweeps": "tcgen05" if tc else "cuda cores",
             "iterations_min_max": [int(its.min()), int(its.max())], "rc": rc,
-            "single_rhs_fp32_vcycle_ms": float(np.mean(single)),
-            "speedup_vs_single_solves": R * float(np.mean(single)) / ms}
+            "single_rhs_fp32_vcycle_ms": float(np.mean(single)) if single else None,
+            "speedup_vs_single_solves": R * float(np.mean(single)) / ms if single else None}
         del S
+    return out
+
+
+def extra_adjoint(pkg, dev, stream):
+    import torch
+    from synthetic import face_neighbors, kuhn_cube, sin_source, smoothed_lognormal_kappa
+    out = {}
     # ---- differentiable solve
     from paper_2012_08024_gb300.autograd import CDGSolve, SolverCache
     mesh = kuhn_cube(24)
@@ -301,9 +333,19 @@ def main():
                     help="skip the batched / multi-RHS / adjoint workloads")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="override the workload's V-cycle precision")
+    ap.add_argument("--only-extra", default=None,
+                    choices=["batched", "multi_rhs", "adjoint", "multi_rhs_bf16", "multi_rhs_bf16_cuda_cores"],
+                    help="run one extra workload alone and print its numbers (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_extra:
+        import torch
+        import paper_2012_08024_gb300 as pkg
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps(run_extras(pkg, dev, torch.cuda.current_stream(dev), None, only=args.only_extra)))
         return
     import torch
     ws, rank, local = dist_info()

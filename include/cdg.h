@@ -106,6 +106,10 @@ typedef struct {
                                A_0 is then non-symmetric: needs krylov = 1, nrhs = 0, no
                                batched handle, no adjoint.  Default 0 (Poisson). */
   double velocity[3];       /* v (first dim entries used) */
+  int32_t tensor_cores;     /* 1 (default): with precision 2, cdg_solve_multi runs the V-cycle's
+                               smoother sweeps on the tcgen05 tensor cores (BF16 blocks exact in
+                               TF32, x split into two TF32 parts: FP32 accuracy); 0: CUDA cores.
+                               A wait that reaches its limit returns CDG_ETIMEOUT. */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16

@@ -40,7 +40,7 @@ class cdg_options(C.Structure):
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32),
-                ("beta", C.c_double), ("velocity", C.c_double * 3)]
+                ("beta", C.c_double), ("velocity", C.c_double * 3), ("tensor_cores", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -139,7 +139,7 @@ class Solver:
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
                  krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False,
-                 beta: float = 0.0, velocity=(0.0, 0.0, 0.0)):
+                 beta: float = 0.0, velocity=(0.0, 0.0, 0.0), tensor_cores: bool = True):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -160,6 +160,7 @@ class Solver:
         o.krylov, o.restart, o.autotune = KRYLOV[krylov], restart, int(autotune)
         o.pmg = int(pmg)
         o.beta = beta
+        o.tensor_cores = int(tensor_cores)
         vel = list(velocity) + [0.0] * (3 - len(velocity))
         for c in range(3):
             o.velocity[c] = float(vel[c])

@@ -215,6 +215,7 @@ void cdg_default_options(cdg_options* o) {
   o->krylov = 0;
   o->restart = 50;
   o->autotune = 1;
+  o->tensor_cores = 1;
 }
 
 const char* cdg_last_error(const cdg_handle* h) {

@@ -320,6 +320,8 @@ struct MR {
   int tile[kMaxLev][4] = {};
   int rows[kMaxLev][4] = {};
   bool tuned = false;
+  bool tc = false;             // smoother sweeps on tcgen05 (BF16 blocks)
+  int* tc_err = nullptr;       // set by a tensor-core kernel whose wait timed out
 };
 
 void mr_tuning(const MR& M, int level, int nlev, int32_t* out) {
@@ -407,6 +409,7 @@ size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* ba
   M.z32 = c.take<float>(nv);
   M.scal = c.take<double>((size_t)R * S_COUNT);
   M.partial = c.take<double>((size_t)2 * M.G * R);
+  M.tc_err = c.take<int>(1);
   return c.off;
 }
 
@@ -473,6 +476,8 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
   auto bsr = [&](int mode, int l, const int* rp, const int* cl, const void* A, const float* x, const float* b,
                  float* y) -> bool {
     const int n = D.lev[l].n;
+    if (mode == 3 && M.tc)
+      return mr_tc_smooth(np, n, R, rp, cl, A, x, b, y, w, M.tc_err, s);
     const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode);
     MR_NP_DISPATCH(np, {
       if (mode == 1)
@@ -656,6 +661,8 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
     }
   }
   cudaMemsetAsync(M.scal, 0, sizeof(double) * (size_t)R * S_COUNT, s);
+  M.tc = M.bf16 && o.tensor_cores != 0 && D.np <= 16;
+  if (M.tc) cudaMemsetAsync(M.tc_err, 0, sizeof(int), s);
   MR_NP_DISPATCH(D.np, mr_rhs_kernel<NP><<<(unsigned)D.ne, T, 0, s>>>(R, D.nq, (int)D.ne, D.perm0, D.rhs_vol, f_q, M.bt));
   count_launch();
   cudaMemsetAsync(M.x, 0, sizeof(double) * nv, s);
@@ -742,11 +749,17 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   }
   mr_out_kernel<<<(unsigned)D.ne, T, 0, s>>>(R, D.np, D.perm0, M.x, (int)D.ne, u);
   count_launch();
+  int tc_err = 0;
+  if (M.tc) cudaMemcpyAsync(&tc_err, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     h->err = std::string("solve_multi: ") + cudaGetErrorString(e);
     return CDG_ECUDA;
+  }
+  if (tc_err) {
+    h->err = "solve_multi: a tensor-core smoother wait reached its iteration limit";
+    return CDG_ETIMEOUT;
   }
   if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
   return status;

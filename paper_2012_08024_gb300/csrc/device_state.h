@@ -161,3 +161,8 @@ void mr_delete(MR* m);
 size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off);
 void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s);
 void mr_tuning(const MR& M, int level, int nlev, int32_t* out);
+
+// device_tc.cu: multi-right-hand-side smoother sweep y = x + omega (bh - x - Ahat x) on
+// tcgen05 tensor cores, Ahat BF16 [nnzb][np][np], vectors [n][np][R]; err set on a wait timeout
+bool mr_tc_smooth(int np, int n, int R, const int* rowptr, const int* col, const void* Ahat_bf16, const float* x,
+                  const float* bh, float* y, float omega, int* err, cudaStream_t s);

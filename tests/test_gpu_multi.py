@@ -53,3 +53,47 @@ def test_bf16_blocks_are_used():
         out[prec] = u.cpu().numpy()
     d = rel(out["bf16"], out["fp32"])
     assert 1e-5 < d < 1e-1, d
+
+
+def test_tensor_core_smoother_matches_cuda_cores():
+    """precision 2 smoother sweeps on tcgen05 (BF16 blocks exact in TF32, x
+    split into two TF32 parts) against the same sweeps on CUDA cores: after
+    one CG iteration the two differ by FP32 summation order only (amplified
+    by the cancellation in x + omega (bh - x - Ahat x)), at least ten times
+    less than the BF16 rounding of the blocks changes the iterate; R = 200
+    spans a full and a ragged 128-column tile."""
+    import torch
+    from paper_2012_08024_gb300 import Solver
+    mesh = jittered_square(10)
+    R = 200
+    out = {}
+    for prec, tc in (("bf16", True), ("bf16", False), ("fp32", False)):
+        S = Solver(mesh, p=3, max_levels=3, nu_pre=2, nu_post=2, precision=prec, nrhs=R, maxit=1,
+                   tensor_cores=tc).bind()
+        xq, _, _ = S.quadrature_points()
+        fq = sine_combination_sources(xq, R, mmax=8, seed0=3)
+        u, hists, its, rc = S.solve_multi(torch.tensor(fq, device="cuda"))
+        out[prec, tc] = u.cpu().numpy()
+    d_tc = rel(out["bf16", True], out["bf16", False])
+    d_bf16 = rel(out["bf16", False], out["fp32", False])
+    print(f"tensor cores vs CUDA cores {d_tc:.3g}, BF16 vs FP32 blocks {d_bf16:.3g}")
+    assert d_tc <= 0.1 * d_bf16, (d_tc, d_bf16)
+
+
+def test_tensor_core_multi_rhs_matches_oracle_p2():
+    import torch
+    from paper_2012_08024_gb300 import Solver
+    mesh = jittered_square(14)
+    R = 150
+    S = Solver(mesh, p=2, max_levels=3, nu_pre=1, nu_post=1, precision="bf16", nrhs=R).bind()
+    xq, _, _ = S.quadrature_points()
+    fq = sine_combination_sources(xq, R, mmax=8, seed0=7)
+    u, hists, its, rc = S.solve_multi(torch.tensor(fq, device="cuda"))
+    assert rc == 0
+    L0 = Level0(mesh, 2)
+    A = L0.matrix().tocsc()
+    lu = spl.splu(A)
+    U = u.cpu().numpy()
+    for r in range(0, R, 7):
+        b = L0.rhs(fq[r])
+        assert rel(U[r].ravel(), lu.solve(b)) <= 1e-9
