@@ -48,6 +48,8 @@ FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured
 # bsr_kernel_tri256_p3_fp64.md) scaled by the block count, exactly 4x (set to None whenever
 # bsr_kernel changes, until it is captured again)
 APPLY_TRAFFIC_BYTES = 4 * 443_725_568
+# the same for the FP32 copy of the operator (None until captured for the current kernel)
+APPLY32_TRAFFIC_BYTES = None
 
 
 def make_mesh(kind, n):
@@ -457,7 +459,25 @@ def main():
         e1.record(stream)
         barrier()
         ms32 = e0.elapsed_time(e1) / args.steps
+        # the FP32 V-cycle's block-sparse kernel (HBM-bound): level-0 FP32 apply
+        x32 = torch.randn(ndof, dtype=torch.float32, device=dev)
+        y32 = torch.empty_like(x32)
+        for _ in range(3):
+            S32.apply_f32(0, x32, y32)
+        e0.record(stream)
+        for _ in range(reps):
+            S32.apply_f32(0, x32, y32)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        k32_us = e0.elapsed_time(e1) / reps * 1e3
+        alg32 = nnzb0 * npb * npb * 4 + nnzb0 * 4 + (S.ne + 1) * 4 + 2 * ndof * 4
+        roof32 = {"bound": "hbm", "achieved": alg32 / (k32_us * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
+                  "frac": alg32 / (k32_us * 1e-6) / 1e9 / peak, "traffic": APPLY32_TRAFFIC_BYTES,
+                  "peak_source": peak_src,
+                  "kernel": "level-0 FP32 block-sparse apply (bsr_kernel<float,%d,0,true>)" % npb,
+                  "alg_bytes_per_launch": alg32, "launch_us": k32_us}
         mixed = {"value": ndof * ws / (ms32 * 1e-3), "ms_per_step": ms32, "iterations": it32,
+                 "roofline_fp32_kernel": roof32,
                  "final_rel_residual": float(h32[-1]),
                  "rel_l2_diff_vs_fp64_solve": float((u32 - u64).norm() / u64.norm()),
                  "speedup_vs_fp64": ms / ms32}

@@ -251,6 +251,9 @@ int cdg_kappa_gradient(cdg_handle* h, const double* lambda, const double* u, con
 /* Per-level operations (device pointers, tree order, FP64): */
 /* y = A_l x  (block-sparse apply, eq. primal_form and Section 4.1) */
 int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream);
+/* y = A_l x with the FP32 copy of A_l that the FP32 V-cycle uses (precision 1 or 2
+ * handles, levels below the coarsest); FP32 vectors.  CDG_EINVAL elsewhere. */
+int cdg_apply_f32(cdg_handle* h, int32_t level, const float* x, float* y, void* stream);
 /* y = b - A_l x */
 int cdg_residual(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
                  void* stream);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "cdg_last_error": (C.c_char_p, [_P]),
     "cdg_query": (_I32, [_P, _P]),
     "cdg_tuning": (_I32, [_P, _I32, _P]),
+    "cdg_apply_f32": (_I32, [_P, _I32, _P, _P, _P]),
     "cdg_quadrature_points": (_I32, [_P, _P, _P, _P]),
     "cdg_export_level": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P]),
     "cdg_export_agglomeration": (_I32, [_P, _I32, _P]),
@@ -336,6 +337,10 @@ class Solver:
 
     def residual(self, level, x, b, y, stream=None):
         self._check(lib().cdg_residual(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+
+    def apply_f32(self, level, x, y, stream=None):
+        """y = A_l x with the FP32 operator copy of the FP32 V-cycle (float32 tensors)."""
+        self._check(lib().cdg_apply_f32(self._h, level, _ptr(x), _ptr(y), _stream_ptr(stream)))
 
     def smooth(self, level, x, b, y, stream=None):
         self._check(lib().cdg_smooth(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))

@@ -430,6 +430,9 @@ int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, doubl
 int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream) {
   return dev_level_op(h, 0, level, x, nullptr, y, stream);
 }
+int cdg_apply_f32(cdg_handle* h, int32_t level, const float* x, float* y, void* stream) {
+  return dev_apply_f32(h, level, x, y, stream);
+}
 int cdg_residual(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
   return dev_level_op(h, 1, level, x, b, y, stream);
 }

@@ -1101,6 +1101,10 @@ static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
     L.unr[ti][3] = pick([&](int u) {
       launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, y, w, nullptr, s, flag, u);
     });
+    if (ti == 1)   // the FP32 apply (cdg_apply_f32)
+      L.unr[1][0] = pick([&](int u) {
+        launch_bsr<T>(0, np, L.n, L.rowptr, L.col, opA<T>(L), x, (const T*)nullptr, y, w, nullptr, s, flag, u);
+      });
   };
   for (int l = 0; l + 1 < D.nlev; ++l) {
     if (D.precision == 0) tune_level(0.0, D.lev[l], l);
@@ -1290,6 +1294,28 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
     return CDG_EINVAL;
   }
   CDG_CHECK_LAUNCH(h, "level op");
+  return CDG_OK;
+}
+
+int dev_apply_f32(cdg_handle* h, int level, const float* x, float* y, void* stream) {
+  if (!h || !x || !y) return CDG_EINVAL;
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  if (level < 0 || level >= D.nlev || !D.lev[level].A32) {
+    h->err = "no FP32 operator on this level (precision 1 or 2 handles, levels below the coarsest)";
+    return CDG_EINVAL;
+  }
+  const DevLevel& L = D.lev[level];
+  const bool aligned = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+  if (!launch_bsr<float>(0, L.np, L.n, L.rowptr, L.col, L.A32, x, (const float*)nullptr, y, h->opt.omega, nullptr,
+                         (cudaStream_t)stream, aligned ? D.scal + S_FLAG : nullptr, unr_of<float>(L, 0))) {
+    h->err = "unsupported n_p";
+    return CDG_EINVAL;
+  }
+  CDG_CHECK_LAUNCH(h, "cdg_apply_f32");
   return CDG_OK;
 }
 

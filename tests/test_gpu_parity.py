@@ -196,3 +196,27 @@ def test_unaligned_caller_vectors(case):
     S.apply(0, xu, yu)
     torch.cuda.synchronize()
     assert rel(yu.cpu().numpy(), ya.cpu().numpy()) <= 1e-14
+
+
+def test_fp32_operator_copy():
+    """cdg_apply_f32: the FP32 copy of A_l that the FP32 V-cycle uses, against the
+    oracle's FP64 operator (FP32 rounding of blocks, vector and sums)."""
+    import torch
+    from paper_2012_08024_gb300 import Solver
+    from oracle.cdg import Level0
+    from oracle.hierarchy import MGHierarchy
+    mesh = jittered_square(16)
+    S = Solver(mesh, p=3, max_levels=3, precision="fp32").bind()
+    H = MGHierarchy(Level0(mesh, 3), max_levels=3)
+    order = H.tree_order()
+    rng = np.random.default_rng(5)
+    for l in range(S.n_levels - 1):
+        n = H.A[l].shape[0]
+        x = rng.standard_normal(n)
+        xt = x.reshape(-1, 10)[order[l]].ravel()
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        S.apply_f32(l, torch.tensor(xt, dtype=torch.float32, device="cuda"), y)
+        yw = np.empty((len(order[l]), 10))
+        yw[order[l]] = y.cpu().numpy().astype(np.float64).reshape(-1, 10)
+        ref = H.A[l] @ x
+        assert rel(yw.ravel(), ref) <= 1e-5, (l, rel(yw.ravel(), ref))
