@@ -48,8 +48,9 @@ FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured
 # bsr_kernel_tri256_p3_fp64.md) scaled by the block count, exactly 4x (set to None whenever
 # bsr_kernel changes, until it is captured again)
 APPLY_TRAFFIC_BYTES = 4 * 443_725_568
-# the same for the FP32 copy of the operator (None until captured for the current kernel)
-APPLY32_TRAFFIC_BYTES = None
+# the same for the FP32 copy of the operator: 223,440,896 bytes captured on the 256 x 256 workload
+# (profiles/bsr_kernel_tri256_p3_fp32.md), scaled by the block count
+APPLY32_TRAFFIC_BYTES = 4 * 223_440_896
 
 
 def make_mesh(kind, n):
