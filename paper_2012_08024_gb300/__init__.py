@@ -50,7 +50,7 @@ class cdg_info(C.Structure):
                 ("n_l", C.c_int64 * CDG_MAX_LEVELS), ("nnzb_l", C.c_int64 * CDG_MAX_LEVELS),
                 ("h_avg", C.c_double), ("C_D", C.c_double), ("device_bytes", C.c_int64),
                 ("setup_seconds", C.c_double * 4), ("n_meshes", C.c_int32),
-                ("np_l", C.c_int32 * CDG_MAX_LEVELS), ("n_plevels", C.c_int32)]
+                ("np_l", C.c_int32 * CDG_MAX_LEVELS), ("n_plevels", C.c_int32), ("solve_graph", C.c_int32)]
 
 
 _lib = None
@@ -237,6 +237,12 @@ class Solver:
         aligned = (base + 255) & ~255
         self._check(lib().cdg_bind_device(self._h, aligned, nbytes, _stream_ptr(None)))
         return self
+
+    def solve_graph(self) -> bool:
+        """True once a CG solve of this handle ran as one CUDA graph launch."""
+        inf = cdg_info()
+        lib().cdg_query(self._h, C.byref(inf))
+        return bool(inf.solve_graph)
 
     def tuning(self):
         """Autotuned launch configuration per level (cdg_tuning)."""

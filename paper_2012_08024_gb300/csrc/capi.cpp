@@ -341,6 +341,7 @@ int cdg_query(const cdg_handle* h, cdg_info* info) {
   info->n_meshes = (int32_t)H.seg_rows[0].size() - 1;
   for (size_t l = 0; l < H.lev.size(); ++l) info->np_l[l] = H.np_l.empty() ? H.np : H.np_l[l];
   info->n_plevels = H.n_plevels;
+  info->solve_graph = dev_solve_graph(h);
   return CDG_OK;
 }
 

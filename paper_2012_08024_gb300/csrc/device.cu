@@ -41,7 +41,7 @@ struct Carver {
 };
 
 size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, char* base, int mr_precision,
-              int gmres_m) {
+              int gmres_m, int maxit) {
   Carver c{base};
   const int np = H.np;
   const int nlev = (int)H.lev.size();
@@ -138,6 +138,9 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   D.gN_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
   D.u_stage = c.take<double>(vecbytes_elems);
   D.scal = c.take<double>((size_t)S_COUNT * D.nseg);
+  D.it_dev = c.take<int>(1);
+  D.iters_dev = c.take<int>(D.nseg);
+  D.hist_dev = c.take<double>((size_t)D.nseg * (maxit + 1));
   D.npartial = std::max<int>(std::max(kDotBlocks, D.nseg * D.bps), (int)((int64_t)ne * np / 64 + 2));
   D.partial = c.take<double>((size_t)D.npartial * 2);
   if (gmres_m > 0) {
@@ -514,6 +517,35 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(const long long* __
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Single-graph solve: mark the segments converged before the loop as closed
+__global__ void hist_init_kernel(int nseg, double* __restrict__ scal) {
+  for (int m = threadIdx.x; m < nseg; m += blockDim.x) scal[(size_t)m * S_COUNT + S_HDONE] = scal[(size_t)m * S_COUNT + S_DONE];
+}
+
+// Single-graph solve, after G1 of iteration it: record ||r||/||b|| and the iteration count of every
+// segment still open (a segment closes in the iteration it converges or breaks down), and keep the
+// loop running while a segment is open and it < maxit.
+__global__ void cg_check_kernel(cudaGraphConditionalHandle cond, int nseg, int maxit, double* __restrict__ scal,
+                                int* __restrict__ it_dev, double* __restrict__ hist, int* __restrict__ iters) {
+  __shared__ int open;
+  if (threadIdx.x == 0) open = 0;
+  __syncthreads();
+  const int it = *it_dev + 1;
+  for (int m = threadIdx.x; m < nseg; m += blockDim.x) {
+    double* sc = scal + (size_t)m * S_COUNT;
+    if (sc[S_HDONE] != 0.0) continue;
+    hist[(size_t)m * (maxit + 1) + it] = sc[S_BB] > 0.0 ? sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
+    iters[m] = it;
+    if (sc[S_DONE] != 0.0) sc[S_HDONE] = 1.0;
+    else atomicOr(&open, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *it_dev = it;
+    cudaGraphSetConditional(cond, (open != 0 && it < maxit) ? 1u : 0u);
+  }
 }
 
 // p = z + beta p (first: p = z)
@@ -1020,7 +1052,7 @@ static int gmres_len(const cdg_options& o) { return o.krylov == 1 ? o.restart : 
 
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
   *bytes = (int64_t)layout(h->H, h->opt.precision == 2 ? 1 : h->opt.precision, h->opt.nrhs, nullptr, nullptr,
-                          h->opt.precision, gmres_len(h->opt));
+                          h->opt.precision, gmres_len(h->opt), h->opt.maxit);
   return CDG_OK;
 }
 
@@ -1029,6 +1061,7 @@ void dev_release(cdg_handle* h) {
     DeviceState& D = *h->dev;
     if (D.g1) cudaGraphExecDestroy(D.g1);
     if (D.g2) cudaGraphExecDestroy(D.g2);
+    if (D.gsolve) cudaGraphExecDestroy(D.gsolve);
     gmres_release(D);
     if (D.stream) {
       cudaStreamSynchronize(D.stream);
@@ -1139,7 +1172,8 @@ int dev_tuning(const cdg_handle* h, int level, int32_t* out) {
 int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   const cdg::Hierarchy& H = h->H;
   const int prec = h->opt.precision == 2 ? 1 : h->opt.precision;
-  const int64_t need = (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision, gmres_len(h->opt));
+  const int64_t need =
+      (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision, gmres_len(h->opt), h->opt.maxit);
   if (bytes < need) {
     h->err = "device buffer too small: need " + std::to_string(need) + " bytes";
     return CDG_ENOMEM;
@@ -1153,7 +1187,7 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   DeviceState& D = *h->dev;
   D.base = (char*)buf;
   D.bytes = bytes;
-  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision, gmres_len(h->opt));
+  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision, gmres_len(h->opt), h->opt.maxit);
   D.precision = h->opt.precision == 2 ? 1 : h->opt.precision;
   cudaStream_t s = (cudaStream_t)stream;
   const int nlev = D.nlev;
@@ -1297,6 +1331,8 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   return CDG_OK;
 }
 
+int dev_solve_graph(const cdg_handle* h) { return h && h->dev && h->dev->gsolve ? 1 : 0; }
+
 int dev_apply_f32(cdg_handle* h, int level, const float* x, float* y, void* stream) {
   if (!h || !x || !y) return CDG_EINVAL;
   if (!h->dev) {
@@ -1394,6 +1430,58 @@ static int capture(cdg_handle* h, int (*part)(cdg_handle*, cudaStream_t), cudaGr
   return CDG_OK;
 }
 
+// The whole CG loop as one executable graph: WHILE (cond) { G1; check; G2 }.  The condition
+// starts at 1 on every launch; the check kernel clears it when every segment has converged or
+// maxit iterations are done, so the loop always ends.  G2 of the last iteration is not needed
+// (it changes z and p only).
+static int capture_solve(cdg_handle* h) {
+  DeviceState& D = *h->dev;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve graph");
+  cudaGraphConditionalHandle cond;
+  e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, e, "solve graph");
+  }
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  const long long before = g_launches.load();
+  e = cudaStreamBeginCaptureToGraph(D.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, e, "solve graph capture");
+  }
+  int rc = cg_part1(h, D.stream);
+  if (rc == CDG_OK) {
+    launch(cg_check_kernel, 1u, 64u, D.stream, cond, D.nseg, h->opt.maxit, D.scal, D.it_dev, D.hist_dev,
+           D.iters_dev);
+    rc = cg_part2(h, D.stream);
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(D.stream, &captured);
+  D.gsolve_kernels = g_launches.load() - before;
+  g_launches.fetch_sub(D.gsolve_kernels, std::memory_order_relaxed);
+  if (rc != CDG_OK || e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return rc != CDG_OK ? rc : cuda_fail(h, e2, "solve graph capture");
+  }
+  e = cudaGraphInstantiate(&D.gsolve, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    D.gsolve = nullptr;
+    return cuda_fail(h, e, "solve graph instantiate");
+  }
+  return CDG_OK;
+}
+
 int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, const double* b_user, double* u,
               int use_u0, double* res_hist, int* iters, int host_ptrs, void* stream) {
   if (!h->dev) {
@@ -1473,9 +1561,51 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
     launch(cg_p_kernel, (unsigned)(nseg * D.bps), kThreads, s, (const long long*)D.seg_dof, D.bps,
            (const double*)D.scal, 1, (const double*)D.z, D.p);
-    if (!D.g1 && (rc = capture(h, cg_part1, &D.g1, &D.g1_kernels)) != CDG_OK) return rc;
-    if (!D.g2 && (rc = capture(h, cg_part2, &D.g2, &D.g2_kernels)) != CDG_OK) return rc;
-    while (true) {
+    if (o.maxit > 0 && !D.gsolve && !D.gsolve_failed && capture_solve(h) != CDG_OK) {
+      D.gsolve_failed = true;   // refused by this driver: keep the host-driven loop
+      h->err.clear();
+      cudaGetLastError();
+    }
+    bool in_graph = false;
+    if (o.maxit > 0 && D.gsolve) {
+      launch(hist_init_kernel, 1u, 64u, s, nseg, D.scal);
+      cudaMemsetAsync(D.it_dev, 0, sizeof(int), s);
+      cudaMemsetAsync(D.iters_dev, 0, sizeof(int) * nseg, s);
+      e = cudaGraphLaunch(D.gsolve, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+      std::vector<double> hh((size_t)nseg * stride);
+      std::vector<int> ih(nseg);
+      int itd = 0;
+      cudaMemcpyAsync(hh.data(), D.hist_dev, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(ih.data(), D.iters_dev, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(&itd, D.it_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(hs.data(), D.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cg");
+      g_launches.fetch_add(D.gsolve_kernels * itd, std::memory_order_relaxed);
+      it = itd;
+      for (int m = 0; m < nseg; ++m) {
+        if (done[m]) continue;
+        iters[m] = ih[m];
+        if (res_hist)
+          for (int k = 1; k <= ih[m]; ++k) res_hist[(size_t)m * stride + k] = hh[(size_t)m * stride + k];
+        const double* sc = &hs[(size_t)m * S_COUNT];
+        if (sc[S_DONE] != 0.0) {
+          done[m] = 1;
+          ++ndone;
+          if (sc[S_BREAK] != 0.0) {
+            status = CDG_EBREAKDOWN;
+            h->err = "CG breakdown on mesh " + std::to_string(m) + " at iteration " + std::to_string(ih[m]) +
+                     ": p^T A p = " + std::to_string(sc[S_PQ]) + ", ||r||^2 = " + std::to_string(sc[S_RR]);
+          }
+        }
+      }
+      if (ndone < nseg) status = CDG_ENOCONV;
+      in_graph = true;
+    }
+    if (!in_graph && !D.g1 && (rc = capture(h, cg_part1, &D.g1, &D.g1_kernels)) != CDG_OK) return rc;
+    if (!in_graph && !D.g2 && (rc = capture(h, cg_part2, &D.g2, &D.g2_kernels)) != CDG_OK) return rc;
+    while (!in_graph) {
       if (it >= o.maxit) {
         status = CDG_ENOCONV;
         break;

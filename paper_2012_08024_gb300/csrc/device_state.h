@@ -13,7 +13,8 @@ constexpr int kThreads = 256;
 constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
 
 // per-segment CG scalars (one row of S_COUNT doubles per mesh of the handle)
-enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, S_FLAG = 15, S_COUNT = 16 };
+// S_HDONE: the segment's residual history is closed (single-graph solve)
+enum Scal { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_BREAK, S_IT, S_HDONE, S_FLAG = 15, S_COUNT = 16 };
 
 struct DevLevel {
   int n = 0;
@@ -89,6 +90,14 @@ struct DeviceState {
   cudaEvent_t ev_in = nullptr;
   cudaGraphExec_t g1 = nullptr, g2 = nullptr;
   long long g1_kernels = 0, g2_kernels = 0;
+  // the whole CG solve as one graph: a conditional WHILE node around [G1, check, G2];
+  // the check kernel records the residual histories and ends the loop on the device
+  cudaGraphExec_t gsolve = nullptr;
+  long long gsolve_kernels = 0;   // kernels per loop iteration
+  bool gsolve_failed = false;     // capture or instantiation refused: two graphs per iteration
+  int* it_dev = nullptr;          // iterations done
+  int* iters_dev = nullptr;       // [nseg]
+  double* hist_dev = nullptr;     // [nseg][maxit+1]
   // multi-right-hand-side solve (cdg_solve_multi): R columns per vector
   int nrhs = 0;
   struct MR* mr = nullptr;   // device_multi.cu

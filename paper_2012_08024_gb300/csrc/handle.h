@@ -34,3 +34,4 @@ int dev_adjoint(cdg_handle* h, int what, const double* lam_user, const double* u
 int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int* iters, void* stream);
 int dev_tuning(const cdg_handle* h, int level, int32_t* out);
 int dev_apply_f32(cdg_handle* h, int level, const float* x, float* y, void* stream);
+int dev_solve_graph(const cdg_handle* h);

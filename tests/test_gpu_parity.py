@@ -220,3 +220,24 @@ def test_fp32_operator_copy():
         yw[order[l]] = y.cpu().numpy().astype(np.float64).reshape(-1, 10)
         ref = H.A[l] @ x
         assert rel(yw.ravel(), ref) <= 1e-5, (l, rel(yw.ravel(), ref))
+
+
+def test_solve_stops_at_maxit_with_the_oracle_history():
+    """The CG loop runs as one graph whose condition the device clears; at maxit
+    it stops with CDG_ENOCONV, and the recorded residual history equals the
+    oracle's PCG history entry by entry."""
+    from paper_2012_08024_gb300 import Solver
+    from oracle.solver import pcg
+    mesh = jittered_square(12)
+    S = Solver(mesh, p=2, max_levels=3, maxit=5, tol=1e-14).bind()
+    oc = OracleCase(mesh, 2, 3)
+    xq, _, _ = S.quadrature_points()
+    fq = sin_source(xq)
+    assert not S.solve_graph()
+    u, hist, it, rc = S.solve(_t(fq))
+    assert S.solve_graph()          # the loop ran as one graph launch, not the host-driven fallback
+    assert rc == 3 and it == 5 and len(hist) == 6
+    uo, ho, ito = pcg(oc.H.A[0], oc.L0.rhs(fq), oc.V.apply, tol=1e-14, maxit=5)
+    assert ito == 5
+    assert np.all(np.abs(hist - np.asarray(ho)) <= 1e-8 * np.asarray(ho))
+    assert rel(u.cpu().numpy().ravel(), uo) <= 1e-10
