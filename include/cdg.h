@@ -127,10 +127,11 @@ typedef struct {
   int32_t n_meshes;         /* 1, or the number of meshes of a batched handle */
   int32_t np_l[CDG_MAX_LEVELS];   /* basis functions per element on each level */
   int32_t n_plevels;        /* p-multigrid: levels of degree p..2 on the fine mesh (0 without) */
-  int32_t solve_graph;      /* 1 once a CG solve has run as a single CUDA graph launch (a conditional
-                               WHILE node around one iteration; convergence and residual histories
-                               decided on the device), 0 before the first solve or when the driver
-                               refused that graph (then two graphs per iteration, host-driven) */
+  int32_t solve_graph;      /* 1 once a CG solve (or a GMRES restart cycle) has run as a single CUDA
+                               graph launch (a conditional WHILE node around one iteration or
+                               Arnoldi step; convergence and residual histories decided on the
+                               device), 0 before the first solve or when the driver refused that
+                               graph (then graphs per iteration or step, host-driven) */
 } cdg_info;
 
 /* Defaults: p=2, gamma=1e4, V(1,1), omega=2/3, 4 levels, seed 0, FP64,

@@ -239,7 +239,7 @@ class Solver:
         return self
 
     def solve_graph(self) -> bool:
-        """True once a CG solve of this handle ran as one CUDA graph launch."""
+        """True once a CG solve (or a GMRES restart cycle) of this handle ran as one CUDA graph launch."""
         inf = cdg_info()
         lib().cdg_query(self._h, C.byref(inf))
         return bool(inf.solve_graph)

@@ -1331,7 +1331,7 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   return CDG_OK;
 }
 
-int dev_solve_graph(const cdg_handle* h) { return h && h->dev && h->dev->gsolve ? 1 : 0; }
+int dev_solve_graph(const cdg_handle* h) { return h && h->dev && (h->dev->gsolve || h->dev->gm_cycle) ? 1 : 0; }
 
 int dev_apply_f32(cdg_handle* h, int level, const float* x, float* y, void* stream) {
   if (!h || !x || !y) return CDG_EINVAL;

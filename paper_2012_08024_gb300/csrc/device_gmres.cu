@@ -283,6 +283,20 @@ __global__ void __launch_bounds__(kThreads) gm_update_kernel(size_t n, size_t ld
   }
 }
 
+// After an Arnoldi step of the single-graph cycle (one thread): count the step,
+// record |g_{j+1}|/||b||, and keep looping while the cycle has room (j < m), the
+// solve is not done and fewer than maxit steps have run.
+__global__ void gm_check_kernel(cudaGraphConditionalHandle cond, GmLayout L, int maxit,
+                                const double* __restrict__ st, const double* __restrict__ scal,
+                                int* __restrict__ it_dev, double* __restrict__ hist) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = *it_dev + 1;
+  *it_dev = it;
+  hist[it] = scal[S_BB] > 0.0 ? sqrt(scal[S_RR] / scal[S_BB]) : 0.0;
+  const int j = step_index(L, st);
+  cudaGraphSetConditional(cond, (scal[S_DONE] == 0.0 && j < L.m && it < maxit) ? 1u : 0u);
+}
+
 // One Arnoldi step (captured once per handle into D.gm_step).
 int arnoldi_step(cdg_handle* h, cudaStream_t s) {
   DeviceState& D = *h->dev;
@@ -333,11 +347,62 @@ int capture_step(cdg_handle* h) {
   return CDG_OK;
 }
 
+// A restart cycle as one executable graph: WHILE (cond) { Arnoldi step; check }.  The
+// condition is 1 at every launch; the check clears it at convergence, breakdown, a full
+// cycle or maxit, and the step counter bounds the loop.
+int capture_cycle(cdg_handle* h) {
+  DeviceState& D = *h->dev;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return dev_cuda_fail(h, e, "GMRES cycle graph");
+  cudaGraphConditionalHandle cond;
+  e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return dev_cuda_fail(h, e, "GMRES cycle graph");
+  }
+  const long long before = launch_count();
+  e = cudaStreamBeginCaptureToGraph(D.stream, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return dev_cuda_fail(h, e, "GMRES cycle capture");
+  }
+  int rc = arnoldi_step(h, D.stream);
+  if (rc == CDG_OK)
+    launch(gm_check_kernel, 1u, 32u, D.stream, cond, GmLayout{D.gm_m}, h->opt.maxit, (const double*)D.gm_st,
+           (const double*)D.scal, D.it_dev, D.hist_dev);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(D.stream, &captured);
+  // captured launches are counted per executed step
+  count_launch(-(launch_count() - before));
+  if (rc != CDG_OK || e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return rc != CDG_OK ? rc : dev_cuda_fail(h, e2, "GMRES cycle capture");
+  }
+  e = cudaGraphInstantiate(&D.gm_cycle, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    D.gm_cycle = nullptr;
+    return dev_cuda_fail(h, e, "GMRES cycle instantiate");
+  }
+  return CDG_OK;
+}
+
 }  // namespace
 
 void gmres_release(DeviceState& D) {
   if (D.gm_step) cudaGraphExecDestroy(D.gm_step);
+  if (D.gm_cycle) cudaGraphExecDestroy(D.gm_cycle);
   D.gm_step = nullptr;
+  D.gm_cycle = nullptr;
 }
 
 int gmres_run(cdg_handle* h, cudaStream_t s, double* res_hist, int* iters) {
@@ -353,6 +418,13 @@ int gmres_run(cdg_handle* h, cudaStream_t s, double* res_hist, int* iters) {
   const unsigned G = kGmBlocks;
   int rc;
   if (!D.gm_step && (rc = capture_step(h)) != CDG_OK) return rc;
+  if (!D.gm_cycle && !D.gm_cycle_failed && capture_cycle(h) != CDG_OK) {
+    D.gm_cycle_failed = true;   // refused by this driver: one graph launch and host read per step
+    h->err.clear();
+    cudaGetLastError();
+  }
+  cudaMemsetAsync(D.it_dev, 0, sizeof(int), s);
+  const long long gk = D.gm_step_kernels + 1;   // kernels per step of the cycle graph
   std::vector<double> hs(S_COUNT);
   auto read = [&](const char* where) -> int {
     cudaMemcpyAsync(hs.data(), D.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
@@ -365,7 +437,23 @@ int gmres_run(cdg_handle* h, cudaStream_t s, double* res_hist, int* iters) {
     launch(gm_init_kernel, G, kThreads, s, n, L, (const double*)D.scal, (const double*)D.r, D.gm_V, D.gm_st);
     int k = 0;
     bool stop = false, broke = false;
-    while (k < D.gm_m && it < o.maxit) {
+    if (D.gm_cycle && it < o.maxit) {
+      const cudaError_t e = cudaGraphLaunch(D.gm_cycle, s);
+      if (e != cudaSuccess) return dev_cuda_fail(h, e, "GMRES graph launch");
+      int itd = it;
+      std::vector<double> hh((size_t)o.maxit + 1);
+      cudaMemcpyAsync(&itd, D.it_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(hh.data(), D.hist_dev, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, s);
+      if ((rc = read("GMRES cycle")) != CDG_OK) return rc;
+      k = itd - it;
+      count_launch(gk * k);
+      if (res_hist)
+        for (int t = it + 1; t <= itd; ++t) res_hist[t] = hh[t];
+      it = itd;
+      broke = hs[S_BREAK] != 0.0;
+      stop = broke || hs[S_DONE] != 0.0;
+    }
+    while (!D.gm_cycle && k < D.gm_m && it < o.maxit) {
       const cudaError_t e = cudaGraphLaunch(D.gm_step, s);
       if (e != cudaSuccess) return dev_cuda_fail(h, e, "GMRES graph launch");
       count_launch(D.gm_step_kernels);

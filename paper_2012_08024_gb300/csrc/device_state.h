@@ -111,6 +111,9 @@ struct DeviceState {
   double* gm_st = nullptr;   // GmLayout(m).size() doubles
   cudaGraphExec_t gm_step = nullptr;
   long long gm_step_kernels = 0;
+  // one restart cycle as one graph: WHILE (cond) { Arnoldi step; check }
+  cudaGraphExec_t gm_cycle = nullptr;
+  bool gm_cycle_failed = false;
 };
 
 // blocks of the GMRES vector kernels (fixed: the dot partials are summed in a fixed order)

@@ -71,6 +71,7 @@ def test_gmres_matches_oracle(case):
     xq, _, _ = S.quadrature_points()
     fq = sin_source(xq)
     u, hist, it, rc = S.solve(_t(fq))
+    assert S.solve_graph()      # every restart cycle ran as one graph launch
     b = L0.rhs(fq)
     uo, ho, ito = gmres(H.A[0], b, V.apply, m=m, tol=tol, maxit=400)
     assert rc == 0, (rc, hist[-3:])
