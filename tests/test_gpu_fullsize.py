@@ -12,6 +12,8 @@ compute element by element.
 * The 256-column solve on the 158 x 158 x 2 mesh (BF16 blocks, tensor-core
   sweeps) against single-column FP64 solves of sampled columns, and the
   64-mesh batch against single-mesh solves of sampled meshes.
+* The 24^3 x 6 differentiable workload: adjoint gradient against central finite
+  differences in 20 directions.
 """
 import numpy as np
 import pytest
@@ -117,3 +119,36 @@ def test_64_mesh_batch_against_single_meshes():
         us, hs, its1, rc1 = S.solve(_t(fq[eo[m]:eo[m + 1]]))
         assert rc1 == 0 and abs(its1 - its[m]) <= 1
         assert rel(ub[eo[m]:eo[m + 1]], us.cpu().numpy()) <= 1e-9, m
+
+
+def test_24_cube_gradient_20_fd_directions():
+    """The differentiable 24^3 x 6 workload as bench.py runs it (p = 2, 5 levels,
+    primal coarsening): dL/dkappa from the adjoint against central finite
+    differences (h = 1e-6) in 20 random directions, each one two fresh set-ups of
+    the whole hierarchy (about 2.5 s each)."""
+    import torch
+    from paper_2012_08024_gb300.autograd import CDGSolve, SolverCache
+    from synthetic import face_neighbors, smoothed_lognormal_kappa
+    mesh = kuhn_cube(24)
+    nb = face_neighbors(mesh)
+    kappa = smoothed_lognormal_kappa(nb, seed=2)
+    kstar = smoothed_lognormal_kappa(nb, seed=3)
+    cache = SolverCache(mesh, p=2, max_levels=5, coarsen="primal", tol=1e-12, maxit=2000)
+    xq = cache.get(torch.tensor(kstar), "cuda").quadrature_points()[0]
+    fq = _t(sin_source(xq))
+    with torch.no_grad():
+        ut = CDGSolve.apply(fq, torch.tensor(kstar, device="cuda"), cache)
+
+    def loss(kap):
+        with torch.no_grad():
+            return float(((CDGSolve.apply(fq, torch.tensor(kap, device="cuda"), cache) - ut) ** 2).sum())
+    k = torch.tensor(kappa, device="cuda", requires_grad=True)
+    L = ((CDGSolve.apply(fq, k, cache) - ut) ** 2).sum()
+    L.backward()
+    g = k.grad.cpu().numpy()
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for _ in range(20):
+        d = rng.standard_normal(mesh.n_elements)
+        fd = (loss(kappa + h * d) - loss(kappa - h * d)) / (2 * h)
+        assert abs(fd - g @ d) <= 1e-5 * np.linalg.norm(g) * np.linalg.norm(d), (fd, g @ d)
