@@ -339,6 +339,9 @@ def main():
                     help="skip the batched / multi-RHS / adjoint workloads")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="override the workload's V-cycle precision")
+    ap.add_argument("--per-iteration-graphs", action="store_true",
+                    help="run the CG loop as graphs per iteration half with a host read each (the same "
+                         "kernels; the form a kernel profiler lists launch by launch)")
     ap.add_argument("--only-extra", default=None,
                     choices=["batched", "multi_rhs", "adjoint", "multi_rhs_bf16", "multi_rhs_bf16_cuda_cores"],
                     help="run one extra workload alone and print its numbers (for profiling)")
@@ -371,7 +374,7 @@ def main():
     mesh = make_mesh(kind, n)
     t0 = time.perf_counter()
     S = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10, maxit=500,
-                   coarsen=coarsen)
+                   coarsen=coarsen, single_graph=not args.per_iteration_graphs)
     setup_s = time.perf_counter() - t0
     S.bind(dev)
     xq, _, _ = S.quadrature_points()

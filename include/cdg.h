@@ -106,6 +106,11 @@ typedef struct {
                                A_0 is then non-symmetric: needs krylov = 1, nrhs = 0, no
                                batched handle, no adjoint.  Default 0 (Poisson). */
   double velocity[3];       /* v (first dim entries used) */
+  int32_t solve_graph;      /* 1 (default): cdg_solve runs the whole CG loop (GMRES: each restart
+                               cycle) as one CUDA graph launch with a conditional WHILE node;
+                               0: host-driven loop, graphs per iteration half (per Arnoldi step),
+                               one host read each.  Same kernels, same order, bit-identical
+                               results; 0 is the form that kernel profilers list launch by launch */
   int32_t tensor_cores;     /* 1 (default): with precision 2, cdg_solve_multi runs the V-cycle's
                                smoother sweeps on the tcgen05 tensor cores (BF16 blocks exact in
                                TF32, x split into two TF32 parts: FP32 accuracy); 0: CUDA cores.

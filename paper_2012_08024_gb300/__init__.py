@@ -40,7 +40,8 @@ class cdg_options(C.Structure):
                 ("enumeration", C.c_void_p), ("kappa", C.c_void_p), ("coarsen", C.c_int32),
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32),
-                ("beta", C.c_double), ("velocity", C.c_double * 3), ("tensor_cores", C.c_int32)]
+                ("beta", C.c_double), ("velocity", C.c_double * 3), ("solve_graph", C.c_int32),
+                ("tensor_cores", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -140,7 +141,8 @@ class Solver:
                  switch_kind: int = 0, face_switch=None, enumeration=None, kappa=None,
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
                  krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False,
-                 beta: float = 0.0, velocity=(0.0, 0.0, 0.0), tensor_cores: bool = True):
+                 beta: float = 0.0, velocity=(0.0, 0.0, 0.0), tensor_cores: bool = True,
+                 single_graph: bool = True):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -162,6 +164,7 @@ class Solver:
         o.pmg = int(pmg)
         o.beta = beta
         o.tensor_cores = int(tensor_cores)
+        o.solve_graph = int(single_graph)
         vel = list(velocity) + [0.0] * (3 - len(velocity))
         for c in range(3):
             o.velocity[c] = float(vel[c])
@@ -381,7 +384,8 @@ class BatchSolver(Solver):
 
     def __init__(self, meshes, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
-                 switch_kind: int = 0, coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500):
+                 switch_kind: int = 0, coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500,
+                 single_graph: bool = True):
         L = lib()
         keep, ms = [], (cdg_mesh * len(meshes))()
         for i, mesh in enumerate(meshes):
@@ -399,6 +403,7 @@ class BatchSolver(Solver):
         o.max_levels, o.seed = max_levels, seed
         o.precision, o.switch_kind = PRECISION[precision], switch_kind
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
+        o.solve_graph = int(single_graph)
         h = C.c_void_p()
         rc = L.cdg_create_batched(ms, len(meshes), C.byref(o), C.byref(h))
         if rc:

@@ -216,6 +216,7 @@ void cdg_default_options(cdg_options* o) {
   o->restart = 50;
   o->autotune = 1;
   o->tensor_cores = 1;
+  o->solve_graph = 1;
 }
 
 const char* cdg_last_error(const cdg_handle* h) {

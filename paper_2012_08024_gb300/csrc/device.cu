@@ -1561,13 +1561,13 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     if ((rc = dot_to(h, D.r, D.z, nullptr, 2, s)) != CDG_OK) return rc;
     launch(cg_p_kernel, (unsigned)(nseg * D.bps), kThreads, s, (const long long*)D.seg_dof, D.bps,
            (const double*)D.scal, 1, (const double*)D.z, D.p);
-    if (o.maxit > 0 && !D.gsolve && !D.gsolve_failed && capture_solve(h) != CDG_OK) {
+    if (o.solve_graph && o.maxit > 0 && !D.gsolve && !D.gsolve_failed && capture_solve(h) != CDG_OK) {
       D.gsolve_failed = true;   // refused by this driver: keep the host-driven loop
       h->err.clear();
       cudaGetLastError();
     }
     bool in_graph = false;
-    if (o.maxit > 0 && D.gsolve) {
+    if (o.solve_graph && o.maxit > 0 && D.gsolve) {
       launch(hist_init_kernel, 1u, 64u, s, nseg, D.scal);
       cudaMemsetAsync(D.it_dev, 0, sizeof(int), s);
       cudaMemsetAsync(D.iters_dev, 0, sizeof(int) * nseg, s);

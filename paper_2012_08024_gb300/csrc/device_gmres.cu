@@ -418,7 +418,7 @@ int gmres_run(cdg_handle* h, cudaStream_t s, double* res_hist, int* iters) {
   const unsigned G = kGmBlocks;
   int rc;
   if (!D.gm_step && (rc = capture_step(h)) != CDG_OK) return rc;
-  if (!D.gm_cycle && !D.gm_cycle_failed && capture_cycle(h) != CDG_OK) {
+  if (o.solve_graph && !D.gm_cycle && !D.gm_cycle_failed && capture_cycle(h) != CDG_OK) {
     D.gm_cycle_failed = true;   // refused by this driver: one graph launch and host read per step
     h->err.clear();
     cudaGetLastError();

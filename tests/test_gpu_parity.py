@@ -241,3 +241,23 @@ def test_solve_stops_at_maxit_with_the_oracle_history():
     assert ito == 5
     assert np.all(np.abs(hist - np.asarray(ho)) <= 1e-8 * np.asarray(ho))
     assert rel(u.cpu().numpy().ravel(), uo) <= 1e-10
+
+
+@pytest.mark.parametrize("krylov,precision", [("cg", "fp64"), ("cg", "fp32"), ("gmres", "fp64")])
+def test_single_graph_and_host_driven_loops_are_identical(krylov, precision):
+    """The one-graph solve (conditional WHILE node) and the host-driven loop run
+    the same kernels in the same order: identical iterates, histories and counts."""
+    from paper_2012_08024_gb300 import Solver
+    mesh = jittered_square(14)
+    kw = dict(p=2, max_levels=3, precision=precision, krylov=krylov)
+    if krylov == "gmres":
+        kw.update(nu_pre=0, nu_post=3, restart=10, tol=1e-10)
+    out = []
+    for single in (True, False):
+        S = Solver(mesh, single_graph=single, **kw).bind()
+        u, hist, it, rc = S.solve(_t(sin_source(S.quadrature_points()[0])))
+        assert rc == 0 and S.solve_graph() == single
+        out.append((u.cpu().numpy(), hist, it))
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
