@@ -124,6 +124,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself without a
+    process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, ms: float) -> float:
+    """Replicas (weak scaling): every rank solves its own copy, so the whole job
+    processes world_size x the units in the slowest rank's time."""
+    return units_per_rank * world_size / (ms * 1e-3)
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -406,12 +423,8 @@ def main():
         e1.record(stream)
         barrier()
     launches = pkg.kernel_launches() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ndof * ws / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    value = whole_job_rate(ndof, ws, ms)
     # ---- end to end through the C ABI with pinned host buffers
     fq_pin = torch.tensor(fq_host).pin_memory()
     u_pin = torch.empty((S.ne, S.np_), dtype=torch.float64).pin_memory()
@@ -430,11 +443,7 @@ def main():
         solve_host()
     e1.record(stream)
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     # ---- dominant kernel: level-0 FP64 block-sparse apply, timed on the launching stream
     x0 = torch.randn(ndof, dtype=torch.float64, device=dev)
     y0 = torch.empty_like(x0)
@@ -573,7 +582,7 @@ def main():
                      "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
                      "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
                      "hbm_frac": achieved / peak},
-        "e2e": {"value": ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
+        "e2e": {"value": whole_job_rate(ndof, ws, ms_e2e), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
         "mixed_fp32_vcycle": mixed,
         "paper_solver_gmres50_v03_tol1e-8": paper_solver,
