@@ -261,3 +261,19 @@ def test_single_graph_and_host_driven_loops_are_identical(krylov, precision):
     assert out[0][2] == out[1][2]
     assert np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_tetrahedral_flux_coarsening_needs_more_iterations():
+    """Beyond the paper (2D only): on the Kuhn-split cube the flux-coarsened
+    hierarchy needs clearly more PCG iterations than primal coarsening (oracle,
+    8^3 x 6, p = 1, V(1,1): 120 against 80), the reverse of the 2D result."""
+    from paper_2012_08024_gb300 import Solver
+    mesh = kuhn_cube(12)
+    its = {}
+    for coarsen in ("flux", "primal"):
+        S = Solver(mesh, p=1, max_levels=6, coarsen=coarsen, maxit=1000).bind()
+        u, hist, it, rc = S.solve(_t(sin_source(S.quadrature_points()[0])))
+        assert rc == 0
+        its[coarsen] = it
+    print("12^3 x 6, p = 1, V(1,1):", its)
+    assert its["flux"] >= 1.25 * its["primal"], its
