@@ -4,7 +4,8 @@ the library's C++ set-up and the oracle share no code, so agreement pins both.
 * Algorithm 2 agglomeration: parents of every level bit-identical;
 * tree numbering bit-identical (children of every agglomerate contiguous);
 * A_l on every level (flux coarsening, Section 4.1) within 1e-12 relative;
-* transfer blocks L_K (Section 3.4) within 1e-12;
+* transfer blocks L_K (Section 3.4) within 1e-12, and upper triangular up to
+  rounding for every supported degree;
 * quadrature points (R3) and boundary-face order / tags identical;
 * errors: degenerate element and missing Dirichlet boundary are rejected.
 """
@@ -88,6 +89,19 @@ def test_library_setup_matches_oracle(name, mk, kw):
     assert np.abs(xbq - L0.all_boundary_points()).max() < 1e-14
     assert list(btag) == [t for (_, _, t) in L0.topo.boundary]
     assert abs(S.info["C_D"] - L0.C_D) <= 1e-12 * L0.C_D
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6), (3, 1), (3, 2), (3, 3)])
+def test_transfer_blocks_upper_triangular(dim, p):
+    """Below the diagonal only rounding remains; it grows with the degree (the
+    Gram matrices of the monomials worsen) to ~7e-11 of a block at p = 6."""
+    from paper_2012_08024_gb300 import Solver
+    mesh = jittered_square(12, seed=7) if dim == 2 else kuhn_cube(3, seed=7)
+    S = Solver(mesh, p=p, max_levels=4)
+    for l in range(S.n_levels - 1):
+        L = S.export_level(l)["L"]
+        low = np.abs(np.tril(L, -1)).max(axis=(1, 2))
+        assert np.all(low <= 1e-9 * np.abs(L).max(axis=(1, 2))), (l, low.max())
 
 
 def test_agglomeration_bit_exact_larger_mesh():

@@ -7,6 +7,10 @@
   inherited fine faces and switch), and A_l = P_l^T C_0 P_l + G_l^T G_l with
   P_l[K, E] = int_K phi_K psi_E^T the direct level-l -> level-0 injection.
 * Primal coarsening (A_{l+1} = R A_l L) differs from flux coarsening.
+* Every transfer block L_K is upper triangular: with bases graded by degree in
+  (x - c)/h (a scalar h) and orthonormalised in that order, the parent's
+  function j restricted to a child lies in the span of the child's functions
+  0..j (an affine map with isotropic scaling keeps each monomial's leading term).
 """
 import numpy as np
 import pytest
@@ -38,6 +42,12 @@ def test_mass_identity_and_transfer(hier):
         L = hier.L[l]
         assert np.abs(L.T @ L - sp.identity(L.shape[1])).max() < 1e-12
         assert np.abs(hier.restriction(l) - L.T).max() < 1e-12
+
+
+def test_transfer_blocks_upper_triangular(hier):
+    for l in range(hier.n_levels - 1):
+        for LK in hier.Lblk[l]:
+            assert np.abs(np.tril(LK, -1)).max(initial=0.0) <= 1e-12 * np.abs(LK).max()
 
 
 def test_coarse_operators_symmetric_positive(hier):
