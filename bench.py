@@ -46,14 +46,20 @@ WORKLOAD_COARSEN = {"tet48_p2": "primal"}
 METRIC = "solved DOF/s (PCG+V-cycle to 1e-10)"
 HBM_FALLBACK_GBS = 6800.0           # profiling-recipe fallback when no measured peak file exists
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured 1.20
-# DRAM bytes (read + write) of one level-0 FP64 apply of the 512 x 512 p = 3 workload: the ncu
-# capture of the same kernel on the 256 x 256 workload (443,725,568 bytes, profiles/
-# bsr_kernel_tri256_p3_fp64.md) scaled by the block count, exactly 4x (set to None whenever
-# bsr_kernel changes, until it is captured again)
-APPLY_TRAFFIC_BYTES = 4 * 443_725_568
-# the same for the FP32 copy of the operator: 223,440,896 bytes captured on the 256 x 256 workload
-# (profiles/bsr_kernel_tri256_p3_fp32.md), scaled by the block count
-APPLY32_TRAFFIC_BYTES = 4 * 223_440_896
+# DRAM bytes (read + write) of one level-0 apply as ncu captured them on the 256 x 256 p = 3
+# square (523,264 blocks): FP64 443,725,568 (profiles/bsr_kernel_tri256_p3_fp64.md), FP32
+# 223,440,896 (profiles/bsr_kernel_tri256_p3_fp32.md).  Other squares at p = 3 report them scaled by
+# their level-0 block count (the traffic is 1.003-1.005x the algorithmic bytes, which grow with
+# the blocks); other workloads report null.  Set to None whenever bsr_kernel changes, until it is
+# captured again.
+CAPTURED_APPLY = {"blocks": 523_264, "fp64": 443_725_568, "fp32": 223_440_896}
+
+
+def apply_traffic(kind, p, nnzb0, dtype):
+    """Per-launch DRAM traffic of the level-0 apply, from the capture scaled by the block count."""
+    if CAPTURED_APPLY.get(dtype) is None or kind != "square" or p != 3:
+        return None
+    return round(CAPTURED_APPLY[dtype] * nnzb0 / CAPTURED_APPLY["blocks"])
 
 
 def make_mesh(kind, n):
@@ -491,7 +497,7 @@ def main():
         k32_us = e0.elapsed_time(e1) / reps * 1e3
         alg32 = nnzb0 * npb * npb * 4 + nnzb0 * 4 + (S.ne + 1) * 4 + 2 * ndof * 4
         roof32 = {"bound": "hbm", "achieved": alg32 / (k32_us * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
-                  "frac": alg32 / (k32_us * 1e-6) / 1e9 / peak, "traffic": APPLY32_TRAFFIC_BYTES,
+                  "frac": alg32 / (k32_us * 1e-6) / 1e9 / peak, "traffic": apply_traffic(kind, p, nnzb0, "fp32"),
                   "peak_source": peak_src,
                   "kernel": "level-0 FP32 block-sparse apply (bsr_kernel<float,%d,0,true>)" % npb,
                   "alg_bytes_per_launch": alg32, "launch_us": k32_us}
@@ -577,7 +583,7 @@ def main():
                    "l2": "inputs larger than L2 (operator %.2f GB)" % (S.info["device_bytes"] / 1e9)},
         "roofline": {"bound": "alu", "achieved": flops / (k_us * 1e-6) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": flops / (k_us * 1e-6) / 1e12 / FP64_NOMINAL_TFLOPS,
-                     "traffic": APPLY_TRAFFIC_BYTES, "peak_source": "nominal FP64 (recipe table)",
+                     "traffic": apply_traffic(kind, p, nnzb0, "fp64"), "peak_source": "nominal FP64 (recipe table)",
                      "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0,true>)" % npb,
                      "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
                      "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
