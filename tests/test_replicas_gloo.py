@@ -49,3 +49,16 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_captured_apply_traffic_scaling():
+    """The ncu-captured level-0 apply traffic (256 x 256 square, p = 3, 523,264
+    blocks) is reported for other p = 3 squares scaled by their block count, and
+    as null for other mesh families or degrees."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cap = bench.CAPTURED_APPLY
+    assert bench.apply_traffic("square", 3, cap["blocks"], "fp64") == cap["fp64"]
+    assert bench.apply_traffic("square", 3, 2_095_104, "fp32") == round(cap["fp32"] * 2_095_104 / 523_264)
+    assert bench.apply_traffic("cube", 3, 2_095_104, "fp64") is None
+    assert bench.apply_traffic("square", 2, 2_095_104, "fp64") is None
