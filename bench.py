@@ -311,7 +311,7 @@ def extra_adjoint(pkg, dev, stream):
     out["adjoint_24cube"] = {"elements": mesh.n_elements, "dofs": S.info["n_dofs"],
                              "forward_ms": fw, "backward_ms": bw, "kappa_gradient_kernel_ms": kg,
                              "first_forward_with_setup_s": t1 - t0, "first_backward_s": t2 - t1,
-                             "loss": float(loss)}
+                             "loss": float(loss.detach())}
     return out
 
 
