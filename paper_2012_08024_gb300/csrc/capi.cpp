@@ -21,6 +21,30 @@ int fail(cdg_handle* h, int code, const std::string& msg) {
   else g_create_error = msg;
   return code;
 }
+
+// No C++ exception crosses the C ABI: a host allocation that fails inside an
+// entry point (staging vectors, graph bookkeeping) returns CDG_ENOMEM, anything
+// else thrown returns CDG_EINVAL with its message.
+int fail_quiet(cdg_handle* h, int code, const char* msg) noexcept {
+  try {
+    fail(h, code, msg);
+  } catch (...) {
+  }
+  return code;
+}
+
+template <typename F>
+int nothrow(cdg_handle* h, F&& f) noexcept {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail_quiet(h, CDG_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail_quiet(h, CDG_EINVAL, e.what());
+  } catch (...) {
+    return fail_quiet(h, CDG_EINVAL, "unexpected exception");
+  }
+}
 }  // namespace
 
 static int check_options(const cdg_options* opt) {
@@ -230,7 +254,8 @@ int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out) {
   int rc = check_options(opt);
   if (rc == CDG_OK) rc = check_mesh(mesh);
   if (rc != CDG_OK) return rc;
-  cdg_handle* h = new cdg_handle();
+  cdg_handle* h = new (std::nothrow) cdg_handle();
+  if (!h) return fail_quiet(nullptr, CDG_ENOMEM, "host allocation failed");
   h->opt = *opt;
   h->opt.face_switch = nullptr;
   h->opt.enumeration = nullptr;
@@ -253,7 +278,8 @@ int cdg_create_batched(const cdg_mesh* meshes, int32_t n_meshes, const cdg_optio
   int rc = check_options(opt);
   for (int32_t m = 0; rc == CDG_OK && m < n_meshes; ++m) rc = check_mesh(&meshes[m]);
   if (rc != CDG_OK) return rc;
-  cdg_handle* h = new cdg_handle();
+  cdg_handle* h = new (std::nothrow) cdg_handle();
+  if (!h) return fail_quiet(nullptr, CDG_ENOMEM, "host allocation failed");
   h->opt = *opt;
   rc = guarded(h, [&] {
     std::vector<cdg::Hierarchy> subs(n_meshes);
@@ -309,7 +335,7 @@ int cdg_tuning(const cdg_handle* h, int32_t level, int32_t* out) {
     const_cast<cdg_handle*>(h)->err = "level out of range";
     return CDG_EINVAL;
   }
-  return dev_tuning(h, level, out);
+  return nothrow(const_cast<cdg_handle*>(h), [&] { return dev_tuning(h, level, out); });
 }
 
 int cdg_query(const cdg_handle* h, cdg_info* info) {
@@ -401,74 +427,90 @@ int cdg_export_agglomeration(const cdg_handle* h, int32_t level, int64_t* parent
 
 int cdg_bind_device(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   if (!h || !buf) return h ? fail(h, CDG_EINVAL, "buffer is NULL") : CDG_EINVAL;
-  return dev_bind(h, buf, bytes, stream);
+  // an exception thrown part-way leaves no half-bound device state behind
+  bool threw = true;
+  const int rc = nothrow(h, [&] {
+    const int r = dev_bind(h, buf, bytes, stream);
+    threw = false;
+    return r;
+  });
+  if (threw) dev_release(h);
+  return rc;
 }
 
 int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b, void* stream) {
   if (!h || !f_q || !b) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  return dev_rhs(h, f_q, gD, gN, b, true, stream);
+  return nothrow(h, [&] { return dev_rhs(h, f_q, gD, gN, b, true, stream); });
 }
 
 int cdg_solve(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* u, int32_t use_u0,
               double* res_hist, int32_t* iters, int32_t host_pointers, void* stream) {
   if (!h || !f_q || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
-  int rc = dev_solve(h, f_q, gD, gN, nullptr, u, use_u0, res_hist, its.data(), host_pointers, stream);
-  if (iters)
-    for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
-  return rc;
+  return nothrow(h, [&] {
+    std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
+    const int rc = dev_solve(h, f_q, gD, gN, nullptr, u, use_u0, res_hist, its.data(), host_pointers, stream);
+    if (iters)
+      for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
+    return rc;
+  });
 }
 
 int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist, int32_t* iters,
                 void* stream) {
   if (!h || !b || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
-  int rc = dev_solve(h, nullptr, nullptr, nullptr, b, u, use_u0, res_hist, its.data(), 0, stream);
-  if (iters)
-    for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
-  return rc;
+  return nothrow(h, [&] {
+    std::vector<int> its(h->H.seg_rows.empty() ? 1 : h->H.seg_rows[0].size() - 1, 0);
+    const int rc = dev_solve(h, nullptr, nullptr, nullptr, b, u, use_u0, res_hist, its.data(), 0, stream);
+    if (iters)
+      for (size_t m = 0; m < its.size(); ++m) iters[m] = its[m];
+    return rc;
+  });
 }
 
 int cdg_apply(cdg_handle* h, int32_t level, const double* x, double* y, void* stream) {
-  return dev_level_op(h, 0, level, x, nullptr, y, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 0, level, x, nullptr, y, stream); });
 }
 int cdg_apply_f32(cdg_handle* h, int32_t level, const float* x, float* y, void* stream) {
-  return dev_apply_f32(h, level, x, y, stream);
+  return nothrow(h, [&] { return dev_apply_f32(h, level, x, y, stream); });
 }
 int cdg_residual(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
-  return dev_level_op(h, 1, level, x, b, y, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 1, level, x, b, y, stream); });
 }
 int cdg_smooth(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
-  return dev_level_op(h, 2, level, x, b, y, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 2, level, x, b, y, stream); });
 }
 int cdg_restrict(cdg_handle* h, int32_t level, const double* r, double* bc, void* stream) {
-  return dev_level_op(h, 3, level, r, nullptr, bc, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 3, level, r, nullptr, bc, stream); });
 }
 int cdg_prolong(cdg_handle* h, int32_t level, const double* xc, double* x, void* stream) {
-  return dev_level_op(h, 4, level, xc, nullptr, x, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 4, level, xc, nullptr, x, stream); });
 }
 int cdg_coarse_solve(cdg_handle* h, const double* b, double* x, void* stream) {
-  return dev_level_op(h, 5, -1, b, nullptr, x, stream);
+  return nothrow(h, [&] { return dev_level_op(h, 5, -1, b, nullptr, x, stream); });
 }
-int cdg_vcycle(cdg_handle* h, const double* r, double* z, void* stream) { return dev_vcycle(h, r, z, stream); }
+int cdg_vcycle(cdg_handle* h, const double* r, double* z, void* stream) {
+  return nothrow(h, [&] { return dev_vcycle(h, r, z, stream); });
+}
 int cdg_to_tree(cdg_handle* h, const double* user, double* tree, void* stream) {
-  return dev_permute(h, user, tree, true, stream);
+  return nothrow(h, [&] { return dev_permute(h, user, tree, true, stream); });
 }
 int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream) {
-  return dev_permute(h, tree, user, false, stream);
+  return nothrow(h, [&] { return dev_permute(h, tree, user, false, stream); });
 }
 
 int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y, void* stream) {
-  return dev_smooth_static(h, level, x, b, y, stream);
+  return nothrow(h, [&] { return dev_smooth_static(h, level, x, b, y, stream); });
 }
 
 int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int32_t* iters, void* stream) {
   if (!h || !f_q || !u) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  std::vector<int> its(h->opt.nrhs > 0 ? h->opt.nrhs : 1, 0);
-  const int rc = dev_solve_multi(h, f_q, u, res_hist, its.data(), stream);
-  if (iters)
-    for (size_t r = 0; r < its.size() && h->opt.nrhs > 0; ++r) iters[r] = its[r];
-  return rc;
+  return nothrow(h, [&] {
+    std::vector<int> its(h->opt.nrhs > 0 ? h->opt.nrhs : 1, 0);
+    const int rc = dev_solve_multi(h, f_q, u, res_hist, its.data(), stream);
+    if (iters)
+      for (size_t r = 0; r < its.size() && h->opt.nrhs > 0; ++r) iters[r] = its[r];
+    return rc;
+  });
 }
 
 int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,
@@ -480,14 +522,14 @@ int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double*
 
 int cdg_rhs_adjoint(cdg_handle* h, const double* lambda, double* dLdf_q, void* stream) {
   if (!h || !lambda || !dLdf_q) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
-  return dev_adjoint(h, 0, lambda, nullptr, nullptr, dLdf_q, stream);
+  return nothrow(h, [&] { return dev_adjoint(h, 0, lambda, nullptr, nullptr, dLdf_q, stream); });
 }
 
 int cdg_kappa_gradient(cdg_handle* h, const double* lambda, const double* u, const double* gD_q, double* dLdkappa,
                        void* stream) {
   if (!h || !lambda || !u || !dLdkappa) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
   if (h->opt.beta != 0.0) return fail(h, CDG_EINVAL, "no adjoint with convection (A_0 is not symmetric)");
-  return dev_adjoint(h, 1, lambda, u, gD_q, dLdkappa, stream);
+  return nothrow(h, [&] { return dev_adjoint(h, 1, lambda, u, gD_q, dLdkappa, stream); });
 }
 
 int64_t cdg_kernel_launches(void) { return (int64_t)dev_launch_count(); }
