@@ -113,6 +113,25 @@ def kernel_launches() -> int:
     return int(lib().cdg_kernel_launches())
 
 
+def _dvec(t, n: int, name: str, dtype: str = "float64") -> int | None:
+    """Device pointer of a CUDA tensor of `dtype` holding at least n contiguous
+    elements (None passes through for nullable arguments).  A host tensor, a
+    wrong dtype or a short buffer raises here instead of reaching a kernel."""
+    if t is None:
+        return None
+    import torch
+    want = getattr(torch, dtype)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    if t.dtype != want:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {want}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: the tensor must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {n} required")
+    return t.data_ptr()
+
+
 def _ptr(a) -> int | None:
     if a is None:
         return None
@@ -262,13 +281,26 @@ class Solver:
     def _dev(self, x):
         return _ptr(x)
 
+    def _lvl(self, level: int) -> int:
+        """Length of a tree-order vector of `level` (0 outside the hierarchy: the
+        library then rejects the level itself)."""
+        if not 0 <= level < self.n_levels:
+            return 0
+        return self.info["n_l"][level] * self.info["np_l"][level]
+
+    def _sizes(self):
+        ne, nbf = self.ne, self.info["n_bfaces"]
+        return ne * self.info["nq"], nbf * self.info["nfq"], ne * self.np_
+
     def solve(self, f_q, gD=None, gN=None, u0=None, stream=None):
         """Device tensors in user order; returns (u, residual history, iterations)."""
         import torch
+        nf, nb, nu = self._sizes()
+        pf, pd, pn = _dvec(f_q, nf, "f_q"), _dvec(gD, nb, "gD"), _dvec(gN, nb, "gN")
         u = torch.empty((self.ne, self.np_), dtype=torch.float64, device=f_q.device) if u0 is None else u0
         hist = np.zeros(self.maxit + 1)
         it = C.c_int32(0)
-        rc = lib().cdg_solve(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(u), 0 if u0 is None else 1,
+        rc = lib().cdg_solve(self._h, pf, pd, pn, _dvec(u, nu, "u0"), 0 if u0 is None else 1,
                              hist.ctypes.data, C.byref(it), 0, _stream_ptr(stream))
         if rc not in (0, 3):
             self._check(rc)
@@ -293,7 +325,8 @@ class Solver:
         u = torch.empty((self.ne, self.np_), dtype=torch.float64, device=b.device)
         hist = np.zeros(self.maxit + 1)
         it = C.c_int32(0)
-        rc = lib().cdg_solve_b(self._h, _ptr(b), _ptr(u), 0, hist.ctypes.data, C.byref(it), _stream_ptr(stream))
+        rc = lib().cdg_solve_b(self._h, _dvec(b, self._sizes()[2], "b"), _ptr(u), 0, hist.ctypes.data, C.byref(it),
+                               _stream_ptr(stream))
         if rc not in (0, 3):
             self._check(rc)
         return u, hist[:it.value + 1], it.value, rc
@@ -306,8 +339,9 @@ class Solver:
         u = torch.empty((R, self.ne, self.np_), dtype=torch.float64, device=f_q.device)
         hist = np.zeros((R, self.maxit + 1))
         its = np.zeros(R, dtype=np.int32)
-        rc = lib().cdg_solve_multi(self._h, _ptr(f_q.contiguous()), _ptr(u), hist.ctypes.data, its.ctypes.data,
-                                   _stream_ptr(stream))
+        f_q = f_q.contiguous()
+        rc = lib().cdg_solve_multi(self._h, _dvec(f_q, R * self._sizes()[0], "f_q"), _ptr(u), hist.ctypes.data,
+                                   its.ctypes.data, _stream_ptr(stream))
         if rc not in (0, 3):
             self._check(rc)
         return u, [hist[r, :its[r] + 1] for r in range(R)], its, rc
@@ -317,8 +351,8 @@ class Solver:
         lam = torch.empty((self.ne, self.np_), dtype=torch.float64, device=dLdu.device)
         hist = np.zeros(self.maxit + 1)
         it = C.c_int32(0)
-        rc = lib().cdg_solve_adjoint(self._h, _ptr(dLdu), _ptr(lam), hist.ctypes.data, C.byref(it),
-                                     _stream_ptr(stream))
+        rc = lib().cdg_solve_adjoint(self._h, _dvec(dLdu, self._sizes()[2], "dLdu"), _ptr(lam), hist.ctypes.data,
+                                     C.byref(it), _stream_ptr(stream))
         if rc not in (0, 3):
             self._check(rc)
         return lam, hist[:it.value + 1], it.value, rc
@@ -326,56 +360,76 @@ class Solver:
     def rhs_adjoint(self, lam, stream=None):
         import torch
         out = torch.empty((self.ne, self.info["nq"]), dtype=torch.float64, device=lam.device)
-        self._check(lib().cdg_rhs_adjoint(self._h, _ptr(lam), _ptr(out), _stream_ptr(stream)))
+        self._check(lib().cdg_rhs_adjoint(self._h, _dvec(lam, self._sizes()[2], "lambda"), _ptr(out),
+                                          _stream_ptr(stream)))
         return out
 
     def kappa_gradient(self, lam, u, gD=None, stream=None):
         import torch
         out = torch.empty(self.ne, dtype=torch.float64, device=lam.device)
-        self._check(lib().cdg_kappa_gradient(self._h, _ptr(lam), _ptr(u), _ptr(gD), _ptr(out), _stream_ptr(stream)))
+        _, nb, nu = self._sizes()
+        self._check(lib().cdg_kappa_gradient(self._h, _dvec(lam, nu, "lambda"), _dvec(u, nu, "u"),
+                                             _dvec(gD, nb, "gD"), _ptr(out), _stream_ptr(stream)))
         return out
 
     def rhs(self, f_q, gD=None, gN=None, stream=None):
         import torch
         b = torch.empty((self.ne, self.np_), dtype=torch.float64, device=f_q.device)
-        self._check(lib().cdg_rhs(self._h, _ptr(f_q), _ptr(gD), _ptr(gN), _ptr(b), _stream_ptr(stream)))
+        nf, nb, _ = self._sizes()
+        self._check(lib().cdg_rhs(self._h, _dvec(f_q, nf, "f_q"), _dvec(gD, nb, "gD"), _dvec(gN, nb, "gN"), _ptr(b),
+                                  _stream_ptr(stream)))
         return b
 
     def apply(self, level, x, y, stream=None):
-        self._check(lib().cdg_apply(self._h, level, _ptr(x), _ptr(y), _stream_ptr(stream)))
+        n = self._lvl(level)
+        self._check(lib().cdg_apply(self._h, level, _dvec(x, n, "x"), _dvec(y, n, "y"), _stream_ptr(stream)))
 
     def residual(self, level, x, b, y, stream=None):
-        self._check(lib().cdg_residual(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+        n = self._lvl(level)
+        self._check(lib().cdg_residual(self._h, level, _dvec(x, n, "x"), _dvec(b, n, "b"), _dvec(y, n, "y"),
+                                       _stream_ptr(stream)))
 
     def apply_f32(self, level, x, y, stream=None):
         """y = A_l x with the FP32 operator copy of the FP32 V-cycle (float32 tensors)."""
-        self._check(lib().cdg_apply_f32(self._h, level, _ptr(x), _ptr(y), _stream_ptr(stream)))
+        n = self._lvl(level)
+        self._check(lib().cdg_apply_f32(self._h, level, _dvec(x, n, "x", "float32"), _dvec(y, n, "y", "float32"),
+                                        _stream_ptr(stream)))
 
     def smooth(self, level, x, b, y, stream=None):
-        self._check(lib().cdg_smooth(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream)))
+        n = self._lvl(level)
+        self._check(lib().cdg_smooth(self._h, level, _dvec(x, n, "x"), _dvec(b, n, "b"), _dvec(y, n, "y"),
+                                     _stream_ptr(stream)))
 
     def smooth_static(self, level, x, b, y, stream=None):
         """cdg_smooth without using the handle's buffer for its intermediate
         (fixed library scratch; see include/cdg.h)."""
-        return lib().cdg_smooth_static(self._h, level, _ptr(x), _ptr(b), _ptr(y), _stream_ptr(stream))
+        n = self._lvl(level)
+        return lib().cdg_smooth_static(self._h, level, _dvec(x, n, "x"), _dvec(b, n, "b"), _dvec(y, n, "y"),
+                                       _stream_ptr(stream))
 
     def restrict(self, level, r, bc, stream=None):
-        self._check(lib().cdg_restrict(self._h, level, _ptr(r), _ptr(bc), _stream_ptr(stream)))
+        self._check(lib().cdg_restrict(self._h, level, _dvec(r, self._lvl(level), "r"),
+                                       _dvec(bc, self._lvl(level + 1), "bc"), _stream_ptr(stream)))
 
     def prolong(self, level, xc, x, stream=None):
-        self._check(lib().cdg_prolong(self._h, level, _ptr(xc), _ptr(x), _stream_ptr(stream)))
+        self._check(lib().cdg_prolong(self._h, level, _dvec(xc, self._lvl(level + 1), "xc"),
+                                      _dvec(x, self._lvl(level), "x"), _stream_ptr(stream)))
 
     def coarse_solve(self, b, x, stream=None):
-        self._check(lib().cdg_coarse_solve(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
+        n = self._lvl(self.n_levels - 1)
+        self._check(lib().cdg_coarse_solve(self._h, _dvec(b, n, "b"), _dvec(x, n, "x"), _stream_ptr(stream)))
 
     def vcycle(self, r, z, stream=None):
-        self._check(lib().cdg_vcycle(self._h, _ptr(r), _ptr(z), _stream_ptr(stream)))
+        n = self._sizes()[2]
+        self._check(lib().cdg_vcycle(self._h, _dvec(r, n, "r"), _dvec(z, n, "z"), _stream_ptr(stream)))
 
     def to_tree(self, user, tree, stream=None):
-        self._check(lib().cdg_to_tree(self._h, _ptr(user), _ptr(tree), _stream_ptr(stream)))
+        n = self._sizes()[2]
+        self._check(lib().cdg_to_tree(self._h, _dvec(user, n, "user"), _dvec(tree, n, "tree"), _stream_ptr(stream)))
 
     def to_user(self, tree, user, stream=None):
-        self._check(lib().cdg_to_user(self._h, _ptr(tree), _ptr(user), _stream_ptr(stream)))
+        n = self._sizes()[2]
+        self._check(lib().cdg_to_user(self._h, _dvec(tree, n, "tree"), _dvec(user, n, "user"), _stream_ptr(stream)))
 
 
 class BatchSolver(Solver):

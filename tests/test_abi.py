@@ -3,6 +3,7 @@ with the binding's signature table covering exactly those (no device calls)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -61,3 +62,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(sname, "sizeof")] == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_binding_rejects_host_tensors_before_the_library():
+    """Device entry points take CUDA tensors only: a host tensor is refused by the
+    binding (ValueError) and never reaches a kernel; None stays None (nullable)."""
+    import torch
+    from paper_2012_08024_gb300 import _dvec
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        _dvec(torch.zeros(4, dtype=torch.float64), 4, "x")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        _dvec(np.zeros(4), 4, "x")
+    assert _dvec(None, 4, "gD") is None

@@ -181,6 +181,26 @@ def test_edge_cases():
     assert rc3 == 3 and it3 == 2 and np.isfinite(u3.cpu().numpy()).all()
 
 
+def test_binding_checks_device_tensors():
+    """A wrong dtype, a short buffer or a non-contiguous view is refused by the
+    binding before the call; the handle stays usable."""
+    import torch
+    from paper_2012_08024_gb300 import Solver
+    S = Solver(jittered_square(6), p=2, max_levels=2).bind()
+    n = S.info["n_l"][0] * S.np_
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(ValueError, match="dtype"):
+        S.apply(0, x.float(), y)
+    with pytest.raises(ValueError, match="at least"):
+        S.apply(0, x[: n - 1], y)
+    with pytest.raises(ValueError, match="contiguous"):
+        S.apply(0, torch.zeros(2 * n, dtype=torch.float64, device="cuda")[::2], y)
+    S.apply(0, x, y)
+    torch.cuda.synchronize()
+    assert not y.abs().max().item()
+
+
 def test_unaligned_caller_vectors(case):
     """Caller vectors that are not 16-byte aligned take the kernel without
     vector loads; results agree with the aligned call."""
