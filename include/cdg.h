@@ -16,7 +16,10 @@
  * Conventions
  *  - Every function returns CDG_OK (0) or one of the error codes below; the
  *    message of the last failure of a handle is cdg_last_error(handle), that of
- *    a failed cdg_create is cdg_last_error(NULL) (per thread).
+ *    a failed cdg_create is cdg_last_error(NULL) (per thread).  No C++
+ *    exception leaves an entry point: a failed host allocation returns
+ *    CDG_ENOMEM (a cdg_bind_device that fails that way leaves the handle
+ *    unbound).
  *  - The caller owns every array it passes; the library copies what it keeps.
  *    A handle owns its host-side hierarchy; its device data lives inside ONE
  *    caller-allocated device buffer given to cdg_bind_device (the library
