@@ -58,7 +58,9 @@ extern "C" {
 typedef struct cdg_handle cdg_handle;
 
 /* Mesh of simplices (Section 2.2: meshes T_h = {K}).  Boundary faces missing
- * from bface are Dirichlet.  Element orientation is free. */
+ * from bface are Dirichlet.  Element orientation is free.  cdg_create returns
+ * CDG_EINVAL for a vertex id out of range, a btag other than 0 or 1, and a
+ * bface entry that is not a boundary face of the mesh or is listed twice. */
 typedef struct {
   int32_t dim;              /* 2 (triangles) or 3 (tetrahedra) */
   int64_t n_vertices;

@@ -436,9 +436,14 @@ void build_mesh(const int dim, i64 nv, const double* xyz, i64 ne, const i64* ele
     std::array<i64, 3> k = {-1, -1, -1};
     for (int j = 0; j < d; ++j) k[j] = bface[i * d + j];
     std::sort(k.begin(), k.begin() + d);
-    tags.push_back({k, btag ? btag[i] : 0});
+    const int t = btag ? btag[i] : 0;
+    if (t != 0 && t != 1) throw std::invalid_argument("btag must be 0 (Dirichlet) or 1 (Neumann)");
+    tags.push_back({k, t});
   }
   std::sort(tags.begin(), tags.end());
+  for (size_t i = 1; i < tags.size(); ++i)
+    if (tags[i].first == tags[i - 1].first) throw std::invalid_argument("a boundary face is listed twice in bface");
+  std::vector<char> tag_used(tags.size(), 0);
   struct IF {
     i64 K1, K2;
     int l1, l2;
@@ -457,13 +462,18 @@ void build_mesh(const int dim, i64 nv, const double* xyz, i64 ne, const i64* ele
     } else if (j - i == 1) {
       int tag = 0;
       auto it = std::lower_bound(tags.begin(), tags.end(), std::make_pair(fk[i].key, INT32_MIN));
-      if (it != tags.end() && it->first == fk[i].key) tag = it->second;
+      if (it != tags.end() && it->first == fk[i].key) {
+        tag = it->second;
+        tag_used[it - tags.begin()] = 1;
+      }
       bfs.push_back({fk[i].K, fk[i].l, tag});
     } else {
       throw std::domain_error("non-manifold face shared by more than two elements");
     }
     i = j;
   }
+  for (char u : tag_used)
+    if (!u) throw std::invalid_argument("a bface entry is not a boundary face of the mesh");
   std::sort(ifs.begin(), ifs.end(), [](const IF& a, const IF& b) {
     return a.K1 != b.K1 ? a.K1 < b.K1 : a.K2 < b.K2;
   });

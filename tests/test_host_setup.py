@@ -133,6 +133,26 @@ def test_errors_are_reported():
     assert e.value.code == 1
 
 
+def test_malformed_meshes_are_rejected():
+    """Inputs that would otherwise be read out of range or silently ignored."""
+    from paper_2012_08024_gb300 import CdgError, Solver
+    m = jittered_square(2)
+    i32, i64 = np.int32, np.int64
+    bad = {
+        "empty mesh": Mesh(2, m.xyz, np.zeros((0, 3), dtype=i64), np.zeros((0, 2), dtype=i64), np.zeros(0, dtype=i32)),
+        "out of range": Mesh(2, m.xyz, np.vstack([m.elem[:-1], [[0, 1, 999]]]), m.bface, m.btag),
+        "btag must be 0": Mesh(2, m.xyz, m.elem, m.bface, np.full(len(m.btag), 5, dtype=i32)),
+        "not a boundary face": Mesh(2, m.xyz, m.elem, np.vstack([m.bface, [[0, 4]]]).astype(i64),
+                                    np.append(m.btag, 0).astype(i32)),
+        "listed twice": Mesh(2, m.xyz, m.elem, np.vstack([m.bface, m.bface[:1]]).astype(i64),
+                             np.append(m.btag, m.btag[0]).astype(i32)),
+    }
+    for msg, mesh in bad.items():
+        with pytest.raises(CdgError) as e:
+            Solver(mesh, p=1)
+        assert e.value.code == 1 and msg in str(e.value), (msg, str(e.value))
+
+
 def test_convection_options_are_checked():
     from paper_2012_08024_gb300 import CdgError, Solver
     m = jittered_square(4)
