@@ -84,8 +84,8 @@ typedef struct {
                                   transfer blocks (FP32 residual operator, block inverses
                                   and arithmetic) */
   int32_t switch_kind;      /* 0: directional consistent switch, 1: natural switch (Section 2.2) */
-  const int8_t* face_switch;   /* nullable: S_{K1}^{K2} per interior face (library face order) */
-  const int64_t* enumeration;  /* nullable: element enumeration N(K) of the natural switch */
+  const int8_t* face_switch;   /* nullable: S_{K1}^{K2} = +1 or -1 per interior face (library face order) */
+  const int64_t* enumeration;  /* nullable: element enumeration N(K) of the natural switch, distinct values */
   const double* kappa;         /* nullable: per-element diffusion coefficient (user order) */
   int32_t coarsen;          /* 0: flux coarsening (Section 4.1), 1: primal A_{l+1} = R A_l L */
   double tol;               /* relative residual ||r||/||b|| to stop CG, default 1e-10 */

@@ -1,5 +1,6 @@
 // C ABI entry points (include/cdg.h): host set-up, queries and exports; the
 // device entry points forward to device.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -53,8 +54,12 @@ static int check_options(const cdg_options* opt) {
     return fail(nullptr, CDG_EINVAL, "max_levels must be in [1, 16]");
   if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->nu_pre + opt->nu_post < 1)
     return fail(nullptr, CDG_EINVAL, "need nu_pre, nu_post >= 0 and at least one smoothing step");
-  if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0))
+  if (!(opt->omega > 0) || !(opt->gamma > 0) || opt->maxit < 0 || !(opt->tol >= 0) || !std::isfinite(opt->omega) ||
+      !std::isfinite(opt->gamma) || !std::isfinite(opt->tol))
     return fail(nullptr, CDG_EINVAL, "bad omega, gamma, tol or maxit");
+  for (int32_t flag : {opt->switch_kind, opt->coarsen, opt->autotune, opt->solve_graph, opt->tensor_cores})
+    if (flag != 0 && flag != 1)
+      return fail(nullptr, CDG_EINVAL, "switch_kind, coarsen, autotune, solve_graph and tensor_cores are 0 or 1");
   if (opt->precision < 0 || opt->precision > 2) return fail(nullptr, CDG_EINVAL, "precision must be 0, 1 or 2");
   if (opt->nrhs < 0 || opt->nrhs > 1024) return fail(nullptr, CDG_EINVAL, "nrhs must be in [0, 1024]");
   if (opt->precision == 2 && opt->nrhs == 0)
@@ -83,6 +88,8 @@ static int check_mesh(const cdg_mesh* mesh) {
     return fail(nullptr, CDG_EINVAL, "empty mesh");
   if (mesh->n_bfaces < 0 || (mesh->n_bfaces > 0 && !mesh->bface))
     return fail(nullptr, CDG_EINVAL, "bad boundary face list");
+  for (int64_t i = 0; i < mesh->n_vertices * mesh->dim; ++i)
+    if (!std::isfinite(mesh->xyz[i])) return fail(nullptr, CDG_EINVAL, "vertex coordinates must be finite");
   return CDG_OK;
 }
 
@@ -103,7 +110,13 @@ static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arr
   o.switch_kind = opt->switch_kind;
   o.coarsen = opt->coarsen;
   const int64_t ne = mesh->n_elements;
-  if (use_arrays && opt->enumeration) o.enumeration.assign(opt->enumeration, opt->enumeration + ne);
+  if (use_arrays && opt->enumeration) {
+    o.enumeration.assign(opt->enumeration, opt->enumeration + ne);
+    std::vector<int64_t> e = o.enumeration;
+    std::sort(e.begin(), e.end());
+    if (std::adjacent_find(e.begin(), e.end()) != e.end())
+      throw std::invalid_argument("the element enumeration must have distinct values");
+  }
   if (use_arrays && opt->kappa) {
     o.kappa.assign(opt->kappa, opt->kappa + ne);
     for (double k : o.kappa)
@@ -115,6 +128,8 @@ static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arr
   if (use_arrays && opt->face_switch) {
     const size_t nif = H.mesh.if_K1.size();
     o.face_switch.assign(opt->face_switch, opt->face_switch + nif);
+    for (int8_t v : o.face_switch)
+      if (v != 1 && v != -1) throw std::invalid_argument("face_switch entries must be +1 or -1");
     cdg::build_mesh(mesh->dim, mesh->n_vertices, mesh->xyz, ne, mesh->elem, mesh->n_bfaces, mesh->bface,
                     mesh->btag, o, H.mesh);
   }

@@ -147,10 +147,35 @@ def test_malformed_meshes_are_rejected():
         "listed twice": Mesh(2, m.xyz, m.elem, np.vstack([m.bface, m.bface[:1]]).astype(i64),
                              np.append(m.btag, m.btag[0]).astype(i32)),
     }
+    xyz = m.xyz.copy()
+    xyz[3, 0] = np.nan
+    bad["must be finite"] = Mesh(2, xyz, m.elem, m.bface, m.btag)
     for msg, mesh in bad.items():
         with pytest.raises(CdgError) as e:
             Solver(mesh, p=1)
         assert e.value.code == 1 and msg in str(e.value), (msg, str(e.value))
+
+
+def test_malformed_options_are_rejected():
+    from paper_2012_08024_gb300 import CdgError, Solver
+    m = jittered_square(3)
+    ne = m.n_elements
+    bad = [
+        (dict(gamma=np.inf), "bad omega"),
+        (dict(omega=np.nan), "bad omega"),
+        (dict(coarsen="flux", switch_kind=2), "are 0 or 1"),
+        (dict(switch_kind=1, enumeration=np.zeros(ne, dtype=np.int64)), "distinct"),
+    ]
+    for kw, msg in bad:
+        with pytest.raises(CdgError) as e:
+            Solver(m, p=1, **kw)
+        assert e.value.code == 1 and msg in str(e.value), (kw, str(e.value))
+    S = Solver(m, p=1)
+    nif = S.info["n_interior_faces"]
+    with pytest.raises(CdgError) as e:
+        Solver(m, p=1, face_switch=np.zeros(nif, dtype=np.int8))
+    assert e.value.code == 1 and "+1 or -1" in str(e.value)
+    Solver(m, p=1, face_switch=np.where(np.arange(nif) % 2 == 0, 1, -1).astype(np.int8))
 
 
 def test_convection_options_are_checked():
