@@ -1,6 +1,9 @@
 """Pins of the oracle's V-cycle (R14) and PCG (R15): the V(nu, nu) cycle is a
 symmetric positive definite linear operator; a one-level cycle is the exact
-solve; PCG agrees with a dense direct solve of A_0 u = b."""
+solve; the cycle equals the textbook multigrid error propagation
+E = S^nu2 (I - L B_{l+1} L^T A_l) S^nu1, S = I - omega D^-1 A_l, written with
+dense matrices (B = (I - E) A^-1, B = A^-1 on the coarsest level), for V(1,1),
+V(2,2) and the paper's V(0,3); PCG agrees with a dense direct solve of A_0 u = b."""
 import numpy as np
 import pytest
 
@@ -24,6 +27,33 @@ def test_vcycle_symmetric_positive(setup):
     B = np.stack([V.apply(e) for e in np.eye(n)], axis=1)
     assert np.abs(B - B.T).max() <= 1e-11 * np.abs(B).max()
     assert np.linalg.eigvalsh((B + B.T) / 2).min() > 0
+
+
+def _closed_form(H, npb, nu1, nu2, omega=2.0 / 3.0):
+    """B_0 from the error propagation recursion, bottom level up."""
+    B = np.linalg.inv(H.A[-1].toarray())
+    for l in range(len(H.A) - 2, -1, -1):
+        A = H.A[l].toarray()
+        n = A.shape[0]
+        D = np.zeros_like(A)
+        for K in range(n // npb):
+            sl = slice(K * npb, (K + 1) * npb)
+            D[sl, sl] = A[sl, sl]
+        S = np.eye(n) - omega * np.linalg.solve(D, A)
+        L = H.L[l].toarray()
+        E = np.linalg.matrix_power(S, nu2) @ (np.eye(n) - L @ B @ L.T @ A) @ np.linalg.matrix_power(S, nu1)
+        B = (np.eye(n) - E) @ np.linalg.inv(A)
+    return B
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 2), (0, 3)])
+def test_vcycle_equals_error_propagation_formula(setup, nu1, nu2):
+    L0, H = setup
+    V = VCycle(H.A, H.L, L0.np_, nu1, nu2)
+    n = H.A[0].shape[0]
+    Bv = np.stack([V.apply(e) for e in np.eye(n)], axis=1)
+    Bc = _closed_form(H, L0.np_, nu1, nu2)
+    assert np.abs(Bv - Bc).max() <= 1e-9 * np.abs(Bc).max()
 
 
 def test_single_level_is_direct_solve(setup):
