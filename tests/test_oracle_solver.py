@@ -3,7 +3,9 @@ symmetric positive definite linear operator; a one-level cycle is the exact
 solve; the cycle equals the textbook multigrid error propagation
 E = S^nu2 (I - L B_{l+1} L^T A_l) S^nu1, S = I - omega D^-1 A_l, written with
 dense matrices (B = (I - E) A^-1, B = A^-1 on the coarsest level), for V(1,1),
-V(2,2) and the paper's V(0,3); PCG agrees with a dense direct solve of A_0 u = b."""
+V(2,2) and the paper's V(0,3); the k-th PCG iterate is the A-norm-optimal
+(Galerkin) solution on the k-dimensional preconditioned Krylov space; PCG agrees
+with a dense direct solve of A_0 u = b."""
 import numpy as np
 import pytest
 
@@ -54,6 +56,30 @@ def test_vcycle_equals_error_propagation_formula(setup, nu1, nu2):
     Bv = np.stack([V.apply(e) for e in np.eye(n)], axis=1)
     Bc = _closed_form(H, L0.np_, nu1, nu2)
     assert np.abs(Bv - Bc).max() <= 1e-9 * np.abs(Bc).max()
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_pcg_iterates_are_krylov_galerkin_solutions(setup, flexible):
+    """With x0 = 0 the k-th PCG iterate minimises the A-norm error over
+    span{Bb, (BA)Bb, ..., (BA)^(k-1) Bb}, B the (fixed, SPD) V-cycle operator;
+    computed here by a dense Galerkin solve on an orthonormalised basis of that
+    space.  The recurrence residual equals b - A x_k."""
+    L0, H = setup
+    V = VCycle(H.A, H.L, L0.np_, 1, 1)
+    A = H.A[0].toarray()
+    n = A.shape[0]
+    B = np.stack([V.apply(e) for e in np.eye(n)], axis=1)
+    b = L0.rhs(sin_source(L0.all_volume_points()))
+    K = [B @ b]
+    for k in range(1, 7):
+        Q, _ = np.linalg.qr(np.stack(K, axis=1))
+        xg = Q @ np.linalg.solve(Q.T @ A @ Q, Q.T @ b)
+        x, hist, it = pcg(H.A[0], b, V.apply, tol=0.0, maxit=k, flexible=flexible)
+        assert it == k
+        e = x - xg
+        assert np.sqrt(e @ A @ e) <= 1e-9 * np.sqrt(xg @ A @ xg), k
+        assert abs(hist[-1] - np.linalg.norm(b - A @ x) / np.linalg.norm(b)) <= 1e-10, k
+        K.append(B @ (A @ K[-1]))
 
 
 def test_single_level_is_direct_solve(setup):
