@@ -39,6 +39,8 @@ CASES = [
     ("tet_p1", lambda: kuhn_cube(2), dict(p=1, max_levels=3)),
     ("tet_p2_seed", lambda: kuhn_cube(2, seed=4), dict(p=2, max_levels=3, seed=11)),
     ("tri_natural", lambda: jittered_square(5), dict(p=1, max_levels=3, switch_kind=1)),
+    ("tri_p4", lambda: jittered_square(4), dict(p=4, max_levels=3)),
+    ("tet_p3", lambda: kuhn_cube(2), dict(p=3, max_levels=3)),
     ("tri_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3,
                                                   kappa=np.exp(np.random.default_rng(1).standard_normal(50)))),
     ("tri_p3_pmg", lambda: jittered_square(8, neumann_axes=(1,)), dict(p=3, max_levels=3, pmg=True)),
