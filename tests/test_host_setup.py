@@ -40,6 +40,7 @@ CASES = [
     ("tet_p2_seed", lambda: kuhn_cube(2, seed=4), dict(p=2, max_levels=3, seed=11)),
     ("tri_natural", lambda: jittered_square(5), dict(p=1, max_levels=3, switch_kind=1)),
     ("tri_p4", lambda: jittered_square(4), dict(p=4, max_levels=3)),
+    ("tri_p6", lambda: jittered_square(3), dict(p=6, max_levels=2)),
     ("tet_p3", lambda: kuhn_cube(2), dict(p=3, max_levels=3)),
     ("tri_kappa", lambda: jittered_square(5), dict(p=2, max_levels=3,
                                                   kappa=np.exp(np.random.default_rng(1).standard_normal(50)))),
@@ -68,6 +69,10 @@ def test_library_setup_matches_oracle(name, mk, kw):
     assert S.n_levels == H.n_levels
     assert S.info["np_l"] == H.nps and S.info["n_plevels"] == H.n_plevels
     order = H.tree_order()
+    # both sides orthonormalise monomials through the Cholesky factor of their Gram
+    # matrix, whose condition number grows with the degree: the two roundings
+    # agree to 1e-12 up to p = 4 and to ~1e-10 at p = 6
+    rtol = 1e-12 if kw["p"] <= 4 else 1e-9
     for l in range(H.n_levels - 1):
         assert list(S.export_agglomeration(l)) == list(H.parent[l])
     for l in range(H.n_levels):
@@ -80,10 +85,10 @@ def test_library_setup_matches_oracle(name, mk, kw):
             P[k * npb:(k + 1) * npb, w * npb:(w + 1) * npb] = np.eye(npb)
         Aor = P @ H.A[l].toarray() @ P.T
         Alib = _dense(ex, n, npb)
-        assert np.abs(Alib - Aor).max() <= 1e-12 * np.abs(Aor).max()
+        assert np.abs(Alib - Aor).max() <= rtol * np.abs(Aor).max()
         if l + 1 < H.n_levels:
             Lor = np.array([H.Lblk[l][w] for w in order[l]])
-            assert np.abs(ex["L"] - Lor).max() <= 1e-12
+            assert np.abs(ex["L"] - Lor).max() <= rtol
             pos = {w: k for k, w in enumerate(order[l + 1])}
             assert list(ex["parent"]) == [pos[H.parent[l][w]] for w in order[l]]
     xq, xbq, btag = S.quadrature_points()
