@@ -90,7 +90,8 @@ typedef struct {
   int32_t coarsen;          /* 0: flux coarsening (Section 4.1), 1: primal A_{l+1} = R A_l L */
   double tol;               /* relative residual ||r||/||b|| to stop CG, default 1e-10 */
   int32_t maxit;            /* CG iteration limit, default 500 */
-  int32_t nrhs;             /* columns of cdg_solve_multi (0 = none), at most 1024 */
+  int32_t nrhs;             /* columns of cdg_solve_multi (0 = none), at most 1024; needs
+                               n_p = 3, 4, 6 or 10 (2D p <= 3, 3D p <= 2) */
   int32_t krylov;           /* outer Krylov method of cdg_solve: 0 CG (A_0 is SPD; needs a
                                symmetric V-cycle, nu_pre = nu_post), 1 restarted GMRES with
                                the V-cycle as right preconditioner (Section 4; flexible form,

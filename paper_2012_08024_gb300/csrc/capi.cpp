@@ -277,6 +277,12 @@ int cdg_create(const cdg_mesh* mesh, const cdg_options* opt, cdg_handle** out) {
   h->opt.kappa = nullptr;
   rc = guarded(h, [&] { build_one(mesh, opt, true, h->H); });
   if (rc != CDG_OK) return rc;
+  // cdg_solve_multi is instantiated for the block sizes of 2D p <= 3 and 3D p <= 2
+  const int np = h->H.np;
+  if (opt->nrhs > 0 && np != 3 && np != 4 && np != 6 && np != 10) {
+    delete h;
+    return fail(nullptr, CDG_EINVAL, "nrhs > 0 (cdg_solve_multi) supports n_p = 3, 4, 6 or 10 (2D p <= 3, 3D p <= 2)");
+  }
   *out = h;
   return CDG_OK;
 }

@@ -644,6 +644,10 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   MR& M = *D.mr;
   const cdg_options& o = h->opt;
   const int R = M.R;
+  if (D.np != 3 && D.np != 4 && D.np != 6 && D.np != 10) {   // cdg_create rejects these already
+    h->err = "unsupported n_p for cdg_solve_multi";
+    return CDG_EINVAL;
+  }
   cudaStream_t cs = (cudaStream_t)stream;
   cudaStream_t s = D.stream;
   cudaEventRecord(D.ev_in, cs);

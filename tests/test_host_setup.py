@@ -183,6 +183,12 @@ def test_malformed_options_are_rejected():
         Solver(m, p=1, face_switch=np.zeros(nif, dtype=np.int8))
     assert e.value.code == 1 and "+1 or -1" in str(e.value)
     Solver(m, p=1, face_switch=np.where(np.arange(nif) % 2 == 0, 1, -1).astype(np.int8))
+    # cdg_solve_multi exists for n_p = 3, 4, 6, 10 only
+    for mesh, p in ((m, 4), (kuhn_cube(2), 3)):
+        with pytest.raises(CdgError) as e:
+            Solver(mesh, p=p, nrhs=8, precision="fp32")
+        assert e.value.code == 1 and "n_p = 3, 4, 6 or 10" in str(e.value)
+    Solver(m, p=3, nrhs=8, precision="fp32")
 
 
 def test_convection_options_are_checked():
