@@ -73,7 +73,8 @@ typedef struct {
 } cdg_mesh;
 
 typedef struct {
-  int32_t p;                /* polynomial degree >= 1 (n_p = C(p+d, d)) */
+  int32_t p;                /* polynomial degree: 1..6 on triangles, 1..3 on tetrahedra
+                               (n_p = C(p+d, d)) */
   double gamma;             /* C_D = gamma / h_avg (Section 2.2), default 1e4 */
   int32_t nu_pre, nu_post;  /* smoothing steps; equal values give a symmetric V-cycle */
   double omega;             /* block-Jacobi damping, default 2/3 (Section 4.3) */

@@ -135,6 +135,9 @@ static void build_one(const cdg_mesh* mesh, const cdg_options* opt, bool use_arr
   }
   H.mono.init(mesh->dim, o.p);
   H.np = H.mono.np;
+  // the device kernels hold one block row in at most one warp and are instantiated
+  // for n_p = 3, 4, 6, 10, 15, 20, 21, 28: every 2D degree up to 6, 3D up to 3
+  if (mesh->dim == 3 && o.p > 3) throw std::invalid_argument("tetrahedra support p <= 3 (n_p <= 20)");
   H.vrule = cdg::simplex_rule(mesh->dim, 2 * o.p);
   H.frule = cdg::simplex_rule(mesh->dim - 1, 2 * o.p);
   H.lev.assign(1, cdg::Level());

@@ -183,6 +183,9 @@ def test_malformed_options_are_rejected():
         Solver(m, p=1, face_switch=np.zeros(nif, dtype=np.int8))
     assert e.value.code == 1 and "+1 or -1" in str(e.value)
     Solver(m, p=1, face_switch=np.where(np.arange(nif) % 2 == 0, 1, -1).astype(np.int8))
+    with pytest.raises(CdgError) as e:
+        Solver(kuhn_cube(2), p=4)
+    assert e.value.code == 1 and "p <= 3" in str(e.value)
     # cdg_solve_multi exists for n_p = 3, 4, 6, 10 only
     for mesh, p in ((m, 4), (kuhn_cube(2), 3)):
         with pytest.raises(CdgError) as e:
