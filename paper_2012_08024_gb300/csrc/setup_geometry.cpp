@@ -245,7 +245,7 @@ static void simplex_coords(const Mesh0& m, i64 K, double* v) {
 
 void basis_eval(const Hierarchy& H, const BasisSet& B, i64 e, const double* x, double* phi) {
   const int d = B.d, np = B.np;
-  double y[3], mval[64];
+  double y[3] = {0.0, 0.0, 0.0}, mval[64];
   const double ih = 1.0 / B.h[e];
   for (int k = 0; k < d; ++k) y[k] = (x[k] - B.c[e * d + k]) * ih;
   H.mono.eval(y, mval);
@@ -259,7 +259,7 @@ void basis_eval(const Hierarchy& H, const BasisSet& B, i64 e, const double* x, d
 
 void basis_grad(const Hierarchy& H, const BasisSet& B, i64 e, const double* x, double* gphi) {
   const int d = B.d, np = B.np;
-  double y[3], g[64 * 3];
+  double y[3] = {0.0, 0.0, 0.0}, g[64 * 3];
   const double ih = 1.0 / B.h[e];
   for (int k = 0; k < d; ++k) y[k] = (x[k] - B.c[e * d + k]) * ih;
   H.mono.grad(y, ih, g);
