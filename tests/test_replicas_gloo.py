@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
 def test_slowest_replica_sets_the_time():
     world = 2
     port = 29500 + os.getpid() % 1000
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
         ms, rate = out[r]
