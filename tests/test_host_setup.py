@@ -123,6 +123,28 @@ def test_agglomeration_bit_exact_larger_mesh():
         assert list(S.export_agglomeration(l)) == Ho.parent[l]
 
 
+@pytest.mark.parametrize("shape", ["square128", "cube16"])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_agglomeration_bit_exact_config_sizes(shape, seed):
+    """Algorithm 2 applied recursively (7 levels) on a 128 x 128 jittered square
+    (32,768 triangles) and a 16^3 x 6 Kuhn cube (24,576 tetrahedra), five mesh
+    and tie-break seeds each: every parent of every level and the tree numbering
+    of the library equal the oracle's."""
+    from paper_2012_08024_gb300 import Solver
+    from oracle.agglomerate import Hierarchy
+    from oracle.mesh import Topology
+    mesh = jittered_square(128, seed=seed) if shape == "square128" else kuhn_cube(16, seed=seed)
+    S = Solver(mesh, p=1, max_levels=7, seed=17 * seed + 1)
+    t = Topology(mesh)
+    Ho = Hierarchy([list(map(int, e)) for e in mesh.elem], t.nbrs, 7, 17 * seed + 1)
+    assert S.n_levels == Ho.n_levels == 7
+    for l in range(Ho.n_levels - 1):
+        assert list(S.export_agglomeration(l)) == Ho.parent[l], l
+    order = Ho.tree_order()
+    for l in range(Ho.n_levels):
+        assert list(S.export_level(l)["perm"]) == list(order[l]), l
+
+
 def test_errors_are_reported():
     from paper_2012_08024_gb300 import CdgError, Solver
     m = jittered_square(2)
