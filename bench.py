@@ -39,13 +39,19 @@ WORKLOADS = {
     "tri256_p3": ("square", 256, 3, 6, 2, "fp64"),
     "tri32_p2": ("square", 32, 2, 4, 1, "fp64"),
     "tet48_p2": ("cube", 48, 2, 6, 2, "fp32"),
+    "tet48_p2_primal": ("cube", 48, 2, 6, 2, "fp32"),
 }
-# coarsening per workload (default flux): on the tetrahedral hierarchies flux coarsening
-# needs 2-3x the iterations of primal coarsening and stalls with the FP32 V-cycle
-WORKLOAD_COARSEN = {"tet48_p2": "primal"}
+# hierarchy options per workload (default: flux coarsening, no p-multigrid front end).  The
+# tetrahedral workload runs the paper's flux coarsening (Section 4.1) behind the p-multigrid
+# front end (Section 4.4): flux-coarsened p = 2 tetrahedral levels alone stall the FP32
+# V-cycle.  Primal coarsening (Section 3.5) is kept as a labelled ablation.
+WORKLOAD_HIERARCHY = {"tet48_p2": dict(coarsen="flux", pmg=True),
+                      "tet48_p2_primal": dict(coarsen="primal", pmg=False)}
 METRIC = "solved DOF/s (PCG+V-cycle to 1e-10)"
 HBM_FALLBACK_GBS = 6800.0           # profiling-recipe fallback when no measured peak file exists
-FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (nominal); an FMA loop measured 1.20
+# GB300 FP64 rate derived from the unit counts and the clock: 152 SMs x 2 FP64 FMA per clock
+# x 2 flops x 2.07 GHz; the roofline divides by the rate the FMA probe measures in the same run
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one level-0 apply as ncu captured them on the 256 x 256 p = 3
 # square (523,264 blocks): FP64 443,725,568 (profiles/bsr_kernel_tri256_p3_fp64.md), FP32
 # 223,440,896 (profiles/bsr_kernel_tri256_p3_fp32.md).  Other squares at p = 3 report them scaled by
@@ -154,10 +160,32 @@ def dist_info():
     return ws, rank, local
 
 
-def cpu_baseline(kind, p, nu, seconds_target=10.0, coarsen="flux"):
-    """Oracle (plain FP64 numpy/scipy) on a bounded sample of the workload: the
-    same generator and discretisation on a 64 x 64 square (8,192 triangles) or
-    a 12^3 cube, oracle set-up untimed, its PCG + V-cycle solve timed."""
+def fp64_fma_peak(pkg, dev, stream):
+    """FP64 FMA rate of this GPU (TFLOP/s), measured with the library's FMA probe
+    (8 independent chains per thread, 8 CTAs of 256 threads per SM), best of 5."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    blocks, iters = 152 * 8, 4096
+    fmas = blocks * 256 * 8 * iters
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    L = pkg.lib()
+    best = 0.0
+    for _ in range(6):
+        e0.record(stream)
+        rc = L.cdg_fp64_fma_probe(blocks, iters, sink.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rc:
+            return None
+        best = max(best, 2.0 * fmas / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def cpu_baseline(kind, p, nu, seconds_target=10.0, coarsen="flux", pmg=False):
+    """Oracle (plain FP64 numpy/scipy, Python, one core) on a bounded sample of
+    the workload: the same generator and discretisation on a 64 x 64 square
+    (8,192 triangles) or a 12^3 cube, oracle set-up untimed, its PCG + V-cycle
+    solve timed."""
     from oracle.cdg import Level0
     from oracle.hierarchy import MGHierarchy
     from oracle.solver import VCycle, pcg
@@ -165,8 +193,8 @@ def cpu_baseline(kind, p, nu, seconds_target=10.0, coarsen="flux"):
     n = 64 if kind == "square" else 12
     mesh = make_mesh(kind, n)
     L0 = Level0(mesh, p)
-    H = MGHierarchy(L0, max_levels=5, coarsen=coarsen)
-    V = VCycle(H.A, H.L, L0.np_, nu, nu)
+    H = MGHierarchy(L0, max_levels=5, coarsen=coarsen, pmg=pmg)
+    V = VCycle(H.A, H.L, H.nps, nu, nu)
     b = L0.rhs(sin_source(L0.all_volume_points()))
     times, its = [], []
     t_end = time.perf_counter() + seconds_target
@@ -179,9 +207,9 @@ def cpu_baseline(kind, p, nu, seconds_target=10.0, coarsen="flux"):
             break
     ndof = H.A[0].shape[0]
     return {"value": ndof / statistics.median(times), "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{'square' if kind == 'square' else 'cube'} n={n} ({mesh.n_elements} elements, "
-                      f"{ndof} dofs), p={p}, {H.n_levels} levels, V({nu},{nu}), tol 1e-10, "
-                      f"{its[0]} iterations, median of {len(times)} solves, set-up untimed"}
+            "sample": f"Python oracle, 1 core, {'square' if kind == 'square' else 'cube'} n={n} sample "
+                      f"({mesh.n_elements} elements, {ndof} dofs), p={p}, {H.n_levels} levels, V({nu},{nu}), "
+                      f"tol 1e-10, {its[0]} iterations, median of {len(times)} solves, set-up untimed"}
 
 
 def _time(fn, stream, reps):
@@ -204,8 +232,10 @@ def run_extras(pkg, dev, stream, barrier, only=None):
     (p = 3) with 256 right-hand sides (sine combinations; FP32 and BF16 V-cycle blocks)
     against 256 single solves estimated from 8; the differentiable 24^3 x 6
     tetrahedra workload (p = 2, smoothed log-normal kappa): forward + adjoint.
-    only: one of "batched", "multi_rhs", "adjoint" (None = all)."""
+    only: one of "latency", "batched", "multi_rhs", "adjoint", "tet48" (None = all)."""
     out = {}
+    if only in (None, "latency"):
+        out.update(extra_latency_tri32(pkg, dev, stream))
     if only in (None, "batched"):
         out.update(extra_batched(pkg, dev, stream))
     if only in (None, "multi_rhs"):
@@ -214,7 +244,54 @@ def run_extras(pkg, dev, stream, barrier, only=None):
         out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))
     if only in (None, "adjoint"):
         out.update(extra_adjoint(pkg, dev, stream))
+    if only in (None, "tet48"):
+        out.update(extra_tet48(pkg, dev, stream))
     return out
+
+
+def extra_tet48(pkg, dev, stream, steps=3):
+    """48^3 x 6 Kuhn cube (663,552 tetrahedra, p = 2, 6.6M dofs): the paper's flux
+    coarsening behind the p-multigrid front end, FP32 V-cycle inside FP64 CG to
+    1e-10, and its distance to the FP64 V-cycle solve of the same hierarchy
+    (one host set-up, bound twice)."""
+    import torch
+    from synthetic import kuhn_cube, sin_source
+    kind, n, p, lv, nu, _ = WORKLOADS["tet48_p2"]
+    t0 = time.perf_counter()
+    S = pkg.Solver(kuhn_cube(n), p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision="fp32", tol=1e-10,
+                   maxit=500, **WORKLOAD_HIERARCHY["tet48_p2"])
+    setup_s = time.perf_counter() - t0
+    S.bind(dev)
+    fq = torch.tensor(sin_source(S.quadrature_points()[0]), device=dev)
+    ms32, (u32, h32, it32, rc32) = _time(lambda: S.solve(fq), stream, steps)
+    u32 = u32.clone()
+    S.set_precision("fp64").bind(dev)
+    ms64, (u64, h64, it64, rc64) = _time(lambda: S.solve(fq), stream, 1)
+    ndof = S.info["n_dofs"]
+    line = {"value": ndof / (ms32 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms32, "iterations": it32, "rc": rc32,
+            "dofs": ndof, "levels": S.n_levels, "np_l": S.info["np_l"], "coarsening": "flux",
+            "front_end": "p-multigrid", "vcycle": "fp32", "final_rel_residual": float(h32[-1]),
+            "fp64_vcycle_ms_per_solve": ms64, "fp64_vcycle_iterations": it64, "fp64_vcycle_rc": rc64,
+            "rel_l2_diff_vs_fp64_vcycle_solve": float((u32 - u64).norm() / u64.norm()),
+            "setup_s": round(setup_s, 2)}
+    del S
+    return {"tet48_p2_flux_pmg_fp32": line}
+
+
+def extra_latency_tri32(pkg, dev, stream):
+    """32 x 32 jittered square (2,048 triangles, p = 2, 12,288 dofs, 4 levels, V(1,1),
+    FP64): solve latency; the operator is L2-resident, so this is a latency number."""
+    import torch
+    from synthetic import sin_source
+    kind, n, p, lv, nu, prec = WORKLOADS["tri32_p2"]
+    S = pkg.Solver(make_mesh(kind, n), p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10,
+                   maxit=500).bind(dev)
+    fq = torch.tensor(sin_source(S.quadrature_points()[0]), device=dev)
+    for _ in range(3):
+        S.solve(fq)
+    ms, (u, h, it, rc) = _time(lambda: S.solve(fq), stream, 20)
+    return {"tri32_p2_latency": {"ms_per_solve": ms, "iterations": it, "rc": rc, "dofs": S.info["n_dofs"],
+                                 "us_per_iteration": ms * 1e3 / max(it, 1)}}
 
 
 def extra_batched(pkg, dev, stream):
@@ -327,8 +404,9 @@ def run_reference(args):
     ns = 64 if kind == "square" else 12
     mesh = make_mesh(kind, ns)
     L0 = Level0(mesh, p)
-    H = MGHierarchy(L0, max_levels=5, coarsen=WORKLOAD_COARSEN.get(args.workload, "flux"))
-    V = VCycle(H.A, H.L, L0.np_, nu, nu)
+    hier = WORKLOAD_HIERARCHY.get(args.workload, {})
+    H = MGHierarchy(L0, max_levels=5, coarsen=hier.get("coarsen", "flux"), pmg=hier.get("pmg", False))
+    V = VCycle(H.A, H.L, H.nps, nu, nu)
     fq = sin_source(L0.all_volume_points())
     for _ in range(args.warmup):
         pcg(H.A[0], L0.rhs(fq), V.apply, tol=1e-10)
@@ -339,7 +417,8 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / args.steps
     ndof = H.A[0].shape[0]
     val = ndof / dt
-    sample = (f"oracle on a {ns}^{2 if kind == 'square' else 3} {'square' if kind == 'square' else 'cube'} sample "
+    sample = (f"Python oracle, 1 core, on a {ns}^{2 if kind == 'square' else 3} "
+              f"{'square' if kind == 'square' else 'cube'} sample "
               f"({mesh.n_elements} elements, {ndof} dofs), p={p}, V({nu},{nu}), each step = rhs + PCG to 1e-10")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s", "n_gpus": args.gpus,
@@ -366,7 +445,8 @@ def main():
                     help="run the CG loop as graphs per iteration half with a host read each (the same "
                          "kernels; the form a kernel profiler lists launch by launch)")
     ap.add_argument("--only-extra", default=None,
-                    choices=["batched", "multi_rhs", "adjoint", "multi_rhs_bf16", "multi_rhs_bf16_cuda_cores"],
+                    choices=["latency", "batched", "multi_rhs", "adjoint", "tet48", "multi_rhs_bf16",
+                             "multi_rhs_bf16_cuda_cores"],
                     help="run one extra workload alone and print its numbers (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -391,13 +471,14 @@ def main():
     import paper_2012_08024_gb300 as pkg
     from synthetic import sin_source
     kind, n, p, lv, nu, prec = WORKLOADS[args.workload]
-    coarsen = WORKLOAD_COARSEN.get(args.workload, "flux")
+    hier = WORKLOAD_HIERARCHY.get(args.workload, {})
+    coarsen, pmg = hier.get("coarsen", "flux"), hier.get("pmg", False)
     if args.precision:
         prec = args.precision
     mesh = make_mesh(kind, n)
     t0 = time.perf_counter()
     S = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10, maxit=500,
-                   coarsen=coarsen, single_graph=not args.per_iteration_graphs)
+                   coarsen=coarsen, pmg=pmg, single_graph=not args.per_iteration_graphs)
     setup_s = time.perf_counter() - t0
     S.bind(dev)
     xq, _, _ = S.quadrature_points()
@@ -470,11 +551,10 @@ def main():
     flops = 2.0 * nnzb0 * npb * npb
     # ---- same workload with the FP32 V-cycle inside the FP64 CG (precision mode 1)
     mixed = None
+    fma_peak = fp64_fma_peak(pkg, dev, stream)
     if prec == "fp64":
         u64 = u.clone()
-        S32 = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision="fp32", tol=1e-10, maxit=500,
-                         coarsen=coarsen)
-        S32.bind(dev)
+        S32 = S.set_precision("fp32").bind(dev)   # same host set-up, FP32 V-cycle
         for _ in range(3):
             u32, h32, it32, rc32 = S32.solve(fq)
         barrier()
@@ -513,9 +593,10 @@ def main():
     if args.extras and prec == "fp64":
         paper_solver = {}
         try:
+            Sg = pkg.Solver(mesh, p=p, max_levels=16, nu_pre=0, nu_post=3, precision="fp64", tol=1e-8,
+                            maxit=500, krylov="gmres", restart=50)
             for pr in ("fp64", "fp32"):
-                Sg = pkg.Solver(mesh, p=p, max_levels=16, nu_pre=0, nu_post=3, precision=pr, tol=1e-8,
-                                maxit=500, krylov="gmres", restart=50).bind(dev)
+                Sg.set_precision(pr).bind(dev)
                 for _ in range(2):
                     ug, hg, itg, rcg = Sg.solve(fq)
                 barrier()
@@ -529,7 +610,7 @@ def main():
                     "value": ndof * ws / (msg * 1e-3), "unit": "DOF/s", "ms_per_step": msg, "iterations": itg,
                     "levels": Sg.n_levels, "rc": rcg, "final_rel_residual": float(hg[-1]),
                     "ms_per_arnoldi_step": msg / max(itg, 1)}
-                del Sg
+            del Sg
         except Exception as e:
             paper_solver["error"] = repr(e)[:300]
     # ---- the same solve with the p-multigrid front end (Section 4.4): degrees p..2 on the
@@ -538,9 +619,10 @@ def main():
     if args.extras and prec == "fp64" and p > 1:
         pmg_line = {}
         try:
+            Sp = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision="fp64", tol=1e-10,
+                            maxit=500, pmg=True)
             for pr in ("fp64", "fp32"):
-                Sp = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=pr, tol=1e-10,
-                                maxit=500, pmg=True).bind(dev)
+                Sp.set_precision(pr).bind(dev)
                 for _ in range(2):
                     up, hp, itp, rcp = Sp.solve(fq)
                 barrier()
@@ -554,7 +636,7 @@ def main():
                     "value": ndof * ws / (msp * 1e-3), "unit": "DOF/s", "ms_per_step": msp, "iterations": itp,
                     "levels": Sp.n_levels, "np_l": Sp.info["np_l"], "rc": rcp, "final_rel_residual": float(hp[-1]),
                     "speedup_vs_fp64_headline": ms / msp}
-                del Sp
+            del Sp
         except Exception as e:
             pmg_line["error"] = repr(e)[:300]
     extras = {}
@@ -569,31 +651,56 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(kind, p, nu, coarsen=coarsen)
+        cpu = cpu_baseline(kind, p, nu, coarsen=coarsen, pmg=pmg)
     clocks = cs.summary()
+    achieved_tf = flops / (k_us * 1e-6) / 1e12
+    fp64_peak = fma_peak if fma_peak else FP64_DERIVED_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak, "traffic": apply_traffic(kind, p, nnzb0, "fp64"),
+                "peak_source": ("measured in this run: FP64 FMA probe (cdg_fp64_fma_probe)" if fma_peak else
+                                "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"),
+                "peak_derived_tflops": FP64_DERIVED_TFLOPS, "frac_of_derived": achieved_tf / FP64_DERIVED_TFLOPS,
+                "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0,true>)" % npb,
+                "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
+                "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
+                "hbm_frac": achieved / peak}
+    if mixed:   # the FP32 V-cycle's block-sparse kernel, HBM-bound
+        r32 = mixed["roofline_fp32_kernel"]
+        roofline.update({"fp32_apply_gbs": r32["achieved"], "fp32_apply_hbm_frac": r32["frac"],
+                         "fp32_apply_launch_us": r32["launch_us"], "fp32_apply_alg_bytes": r32["alg_bytes_per_launch"],
+                         "fp32_apply_traffic": r32["traffic"]})
+    config = {"workload": args.workload, "mesh": f"{kind} {n}", "elements": S.ne, "p": p, "dofs": ndof,
+              "levels": S.n_levels, "n_l": S.info["n_l"], "nnzb_l": S.info["nnzb_l"],
+              "smoother": f"V({nu},{nu}) block Jacobi omega=2/3", "coarsening": coarsen,
+              "p_multigrid_front_end": pmg, "tol": 1e-10, "precision": prec,
+              "iterations": iters[-1], "setup_s": round(setup_s, 3), "parallelism": f"replicas x{ws}",
+              "l2": "inputs larger than L2 (operator %.2f GB)" % (S.info["device_bytes"] / 1e9)}
+    # the other BASELINE workloads' headline numbers, as scalars beside the workload's own
+    lat = extras.get("tri32_p2_latency")
+    if lat:
+        config.update({"tri32_p2_ms_per_solve": lat["ms_per_solve"], "tri32_p2_iterations": lat["iterations"]})
+    t48 = extras.get("tet48_p2_flux_pmg_fp32")
+    if t48:
+        config.update({"tet48_p2_flux_pmg_fp32_ms_per_solve": t48["ms_per_solve"],
+                       "tet48_p2_flux_pmg_fp32_dofs_per_s": t48["value"],
+                       "tet48_p2_flux_pmg_fp32_iterations": t48["iterations"],
+                       "tet48_p2_flux_pmg_fp32_rel_l2_vs_fp64": t48["rel_l2_diff_vs_fp64_vcycle_solve"]})
+    if mixed:
+        config.update({"mixed_fp32_vcycle_ms_per_solve": mixed["ms_per_step"],
+                       "mixed_fp32_vcycle_iterations": mixed["iterations"]})
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": args.workload, "mesh": f"{kind} {n}", "elements": S.ne, "p": p, "dofs": ndof,
-                   "levels": S.n_levels, "n_l": S.info["n_l"], "nnzb_l": S.info["nnzb_l"],
-                   "smoother": f"V({nu},{nu}) block Jacobi omega=2/3", "coarsening": coarsen, "tol": 1e-10,
-                   "precision": prec,
-                   "iterations": iters[-1], "setup_s": round(setup_s, 3), "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (operator %.2f GB)" % (S.info["device_bytes"] / 1e9)},
-        "roofline": {"bound": "alu", "achieved": flops / (k_us * 1e-6) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
-                     "unit": "TFLOP/s", "frac": flops / (k_us * 1e-6) / 1e12 / FP64_NOMINAL_TFLOPS,
-                     "traffic": apply_traffic(kind, p, nnzb0, "fp64"), "peak_source": "nominal FP64 (recipe table)",
-                     "kernel": "level-0 FP64 block-sparse apply (bsr_kernel<double,%d,0,true>)" % npb,
-                     "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": flops, "launch_us": k_us,
-                     "hbm_gbs": achieved, "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
-                     "hbm_frac": achieved / peak},
+        "config": config,
+        "roofline": roofline,
         "e2e": {"value": whole_job_rate(ndof, ws, ms_e2e), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(fq_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
         "mixed_fp32_vcycle": mixed,
         "paper_solver_gmres50_v03_tol1e-8": paper_solver,
         "pmg_front_end": pmg_line,
-        **extras,
+        **{k: v for k, v in extras.items() if k != "tet48_p2_flux_pmg_fp32"},
+        "tet48_p2_flux_pmg_fp32": t48,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -202,6 +202,14 @@ int cdg_export_level(const cdg_handle* h, int32_t level, int64_t* perm, int32_t*
  * parent [n_l] = index of the agglomerate on level l+1 in creation order. */
 int cdg_export_agglomeration(const cdg_handle* h, int32_t level, int64_t* parent);
 
+/* Changes the V-cycle precision of a handle (cdg_options.precision: 0, 1, or 2
+ * for a handle with nrhs) without repeating the host set-up, which does not
+ * depend on it (the paper fixes no precision; this is an execution option of
+ * the library).  Releases the device binding: query cdg_info.device_bytes again
+ * and call cdg_bind_device before the next device call.  Errors: CDG_EINVAL
+ * (bad value, NULL handle). */
+int cdg_set_precision(cdg_handle* h, int32_t precision);
+
 /* Device binding: copies the hierarchy into dev_buffer (>= info.device_bytes
  * bytes, 256-byte aligned) on stream and synchronises it.  Errors: CDG_ENOMEM
  * (buffer too small), CDG_ECUDA. */
@@ -281,7 +289,11 @@ int cdg_smooth(cdg_handle* h, int32_t level, const double* x, const double* b, d
 int cdg_restrict(cdg_handle* h, int32_t level, const double* r, double* bc, void* stream);
 /* x += L xc  (level+1 -> level injection, Section 3.4) */
 int cdg_prolong(cdg_handle* h, int32_t level, const double* xc, double* x, void* stream);
-/* x = A_n^{-1} b on the coarsest level (dense inverse, Section 4.3) */
+/* x = A_n^{-1} b on the coarsest level (direct solve, Section 4.3): the dense
+ * inverse times b, followed in an FP64 handle (precision 0) by one step of
+ * iterative refinement x += A_n^{-1} (b - A_n x) with the block-sparse A_n, so
+ * the result is that of a backward-stable solve (within cond(A_n) eps of a
+ * factorisation-based one).  b and x must not alias. */
 int cdg_coarse_solve(cdg_handle* h, const double* b, double* x, void* stream);
 /* z = V(r): one V(nu_pre, nu_post) cycle on level 0 from a zero guess (R14),
  * in the handle's precision; r, z FP64 tree order. */
@@ -299,14 +311,25 @@ int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream);
  * a fixed device array inside the library (CDG_STATIC_SCRATCH doubles = 8 MiB,
  * held by every GPU that loads the library until the process exits) instead of
  * the handle's buffer; levels with n_l * n_p > CDG_STATIC_SCRATCH are rejected
- * with CDG_EINVAL.  The first call on a device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU (on
+ * with CDG_EINVAL, and so is the coarsest level.  The first call on a device
+ * looks up the array's device address with that device current, and so does
+ * the first call after the current context changed (cudaDeviceReset, another
+ * context made current); make those calls before any stream capture.  All calls share the one array: calls that overlap on the GPU (on
  * different streams, or from different threads) race and must be serialised
  * by the caller.  No device or host memory is allocated by this call. */
 #define CDG_STATIC_SCRATCH (1 << 20)
 int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
                       void* stream);
+
+/* FP64 FMA throughput probe (no counterpart in the paper: it measures the
+ * arithmetic bound of the FP64 block-sparse kernels on the device at hand).
+ * Launches blocks x 256 threads, each running 8 independent FMA chains of
+ * iters steps: blocks * 256 * 8 * iters FMAs in total.  The caller times the
+ * launch on `stream` (e.g. with CUDA events) and divides.  sink: device pointer
+ * to one double that the kernel writes only for inputs that never occur (keeps
+ * the chains live).  Errors: CDG_EINVAL (blocks or iters < 1, NULL sink),
+ * CDG_ECUDA. */
+int cdg_fp64_fma_probe(int32_t blocks, int64_t iters, double* sink, void* stream);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (instrumentation for benchmarks; thread-safe, never reset). */

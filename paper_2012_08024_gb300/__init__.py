@@ -72,6 +72,8 @@ SIGNATURES = {
     "cdg_export_level": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P]),
     "cdg_export_agglomeration": (_I32, [_P, _I32, _P]),
     "cdg_bind_device": (_I32, [_P, _P, _I64, _P]),
+    "cdg_set_precision": (_I32, [_P, _I32]),
+    "cdg_fp64_fma_probe": (_I32, [_I32, _I64, _P, _P]),
     "cdg_rhs": (_I32, [_P, _P, _P, _P, _P, _P]),
     "cdg_solve": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P]),
     "cdg_solve_b": (_I32, [_P, _P, _P, _I32, _P, _P, _P]),
@@ -260,6 +262,17 @@ class Solver:
         self._check(lib().cdg_bind_device(self._h, aligned, nbytes, _stream_ptr(None)))
         return self
 
+    def set_precision(self, precision: str):
+        """Switch the V-cycle precision without repeating the host set-up
+        (cdg_set_precision); releases the device binding, so bind() again."""
+        self._check(lib().cdg_set_precision(self._h, PRECISION[precision]))
+        self.precision = precision
+        self.buffer = None
+        inf = cdg_info()
+        lib().cdg_query(self._h, C.byref(inf))
+        self.info["device_bytes"] = inf.device_bytes
+        return self
+
     def solve_graph(self) -> bool:
         """True once a CG solve (or a GMRES restart cycle) of this handle ran as one CUDA graph launch."""
         inf = cdg_info()
@@ -402,10 +415,11 @@ class Solver:
 
     def smooth_static(self, level, x, b, y, stream=None):
         """cdg_smooth without using the handle's buffer for its intermediate
-        (fixed library scratch; see include/cdg.h)."""
+        (fixed library scratch; see include/cdg.h).  Raises CdgError like the
+        other device methods (a level beyond the fixed scratch: CDG_EINVAL)."""
         n = self._lvl(level)
-        return lib().cdg_smooth_static(self._h, level, _dvec(x, n, "x"), _dvec(b, n, "b"), _dvec(y, n, "y"),
-                                       _stream_ptr(stream))
+        self._check(lib().cdg_smooth_static(self._h, level, _dvec(x, n, "x"), _dvec(b, n, "b"), _dvec(y, n, "y"),
+                                            _stream_ptr(stream)))
 
     def restrict(self, level, r, bc, stream=None):
         self._check(lib().cdg_restrict(self._h, level, _dvec(r, self._lvl(level), "r"),

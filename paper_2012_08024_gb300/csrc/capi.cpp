@@ -462,6 +462,23 @@ int cdg_bind_device(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   return rc;
 }
 
+int cdg_set_precision(cdg_handle* h, int32_t precision) {
+  if (!h) return CDG_EINVAL;
+  if (precision < 0 || precision > 2) return fail(h, CDG_EINVAL, "precision must be 0, 1 or 2");
+  if (precision == 2 && h->opt.nrhs == 0)
+    return fail(h, CDG_EINVAL, "precision 2 (BF16 blocks) is the multi-right-hand-side mode: set nrhs");
+  return nothrow(h, [&] {
+    dev_release(h);
+    h->opt.precision = precision;
+    return CDG_OK;
+  });
+}
+
+int cdg_fp64_fma_probe(int32_t blocks, int64_t iters, double* sink, void* stream) {
+  if (blocks < 1 || iters < 1 || !sink) return CDG_EINVAL;
+  return dev_fma_probe(blocks, iters, sink, stream);
+}
+
 int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b, void* stream) {
   if (!h || !f_q || !b) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
   return nothrow(h, [&] { return dev_rhs(h, f_q, gD, gN, b, true, stream); });

@@ -343,9 +343,10 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(int n, const int* __r
   x[row] = ADD ? x[row] + s : s;
 }
 
-// coarsest solve: x = Ainv_m b on every segment m, one warp per row; each
-// segment has its own dense inverse (row-major, n_m x n_m), FP64 accumulation
-template <typename TI, typename TO>
+// coarsest solve: x = Ainv_m b (ADD: x += Ainv_m b) on every segment m, one
+// warp per row; each segment has its own dense inverse (row-major, n_m x n_m),
+// FP64 accumulation
+template <typename TI, typename TO, bool ADD = false>
 __global__ void coarse_kernel(int nc, const int* __restrict__ crow_seg, const int* __restrict__ crow_off,
                               const long long* __restrict__ cinv_off, const double* __restrict__ Ainv,
                               const TI* __restrict__ b, TO* __restrict__ x) {
@@ -359,7 +360,7 @@ __global__ void coarse_kernel(int nc, const int* __restrict__ crow_seg, const in
   double s = 0.0;
   for (int j = lane; j < nm; j += 32) s = fma(a[j], (double)bm[j], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = (TO)s;
+  if (lane == 0) x[row] = ADD ? (TO)((double)x[row] + s) : (TO)s;
 }
 
 // Between two degrees of the p-multigrid levels (Section 4.4) the orthonormal
@@ -675,6 +676,25 @@ __global__ void rhs_adjoint_kernel(int ne, int nq, const int* __restrict__ perm0
   out[(size_t)perm0[k] * nq + q] = s;
 }
 
+// FP64 FMA throughput probe: 8 independent dependency chains per thread, so
+// the FP64 pipe, not the FMA latency, limits the rate.  The values depend on
+// the runtime seed (nothing folds at compile time); sink is written only if
+// the chains end exactly at a value they cannot reach.
+__global__ void __launch_bounds__(kThreads) fma64_probe_kernel(long long iters, double seed, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + 1e-3 * k + 1e-9 * threadIdx.x;
+  const double m = 0.9999999, c = 1e-7;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.0) *sink = s;
+}
+
 // ------------------------------------------------------------------ launch helpers
 // Every kernel launch of the library goes through here (counted for the
 // benchmark's launch accounting).
@@ -840,6 +860,29 @@ const float* opL<float>(const DevLevel& L) { return L.L32; }
 template <typename T>
 int unr_of(const DevLevel& L, int mode) { return L.unr[sizeof(T) == 8 ? 0 : 1][mode]; }
 
+// Direct solve on the coarsest level (Algorithm 3): x = A_n^{-1} b through the
+// dense inverse.  With the FP64 operator on the device (FP64 V-cycle) one step
+// of iterative refinement follows, x += A_n^{-1} (b - A_n x) with the residual
+// from the block-sparse A_n: an explicit inverse times b is not backward
+// stable, the refined solution is (Skeel 1980), so it agrees with a
+// factorisation-based solve to cond(A_n) eps.  r is a coarsest-level work
+// vector that aliases neither b nor x.
+template <typename T>
+void coarse_solve(DeviceState& D, const T* b, T* x, cudaStream_t s) {
+  const unsigned g = (unsigned)((D.nc * 32 + 255) / 256);
+  launch(coarse_kernel<T, T, false>, g, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off, D.coarse_inv, b, x);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    const DevLevel& C = D.lev[D.nlev - 1];
+    if (!C.A || D.precision != 0) return;   // the work vectors of an FP32 V-cycle hold floats
+    double* r = (double*)C.r;
+    const bool aligned = (((uintptr_t)b | (uintptr_t)x) & 15) == 0;
+    launch_bsr<double>(1, C.np, C.n, C.rowptr, C.col, C.A, x, b, r, 0.0, nullptr, s,
+                       aligned ? D.scal + S_FLAG : nullptr, unr_of<double>(C, 1));
+    launch(coarse_kernel<double, double, true>, g, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off, D.coarse_inv,
+           (const double*)r, x);
+  }
+}
+
 // One V(nu_pre, nu_post) cycle from a zero guess (R14) on levels 0..n, with
 // b0 / z0 the level-0 right-hand side and result (precision T).
 template <typename T>
@@ -847,8 +890,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   const int nlev = D.nlev;
   const double w = o.omega;
   if (nlev == 1) {
-    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off,
-           D.coarse_inv, b0, z0);
+    coarse_solve<T>(D, b0, z0, s);
     return true;
   }
   std::vector<const T*> bl(nlev);
@@ -885,8 +927,7 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
   // coarsest
   {
     const DevLevel& C = D.lev[nlev - 1];
-    launch(coarse_kernel<T, T>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off, D.cinv_off,
-           D.coarse_inv, (const T*)C.b, (T*)C.x);
+    coarse_solve<T>(D, (const T*)C.b, (T*)C.x, s);
   }
   // upward sweep
   for (int l = nlev - 2; l >= 0; --l) {
@@ -997,6 +1038,26 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 double* g_static_ptr[kMaxDevices] = {};
+// the context each cached address belongs to: after cudaDeviceReset, or with
+// another context current, the address is looked up again
+void* g_static_ctx[kMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry-point query (no link
+// dependency on the driver library); nullptr if the query fails
+void* current_context() {
+  using Fn = int (*)(void**);
+  static Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (Fn)f;
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 }  // namespace
 
 int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b, double* y, void* stream) {
@@ -1025,13 +1086,15 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
   }
   double* scratch = nullptr;
   {
-    // once per device, with that device current: the symbol's device address
+    // once per device and context, with that device current: the symbol's device address
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
+    void* ctx = current_context();
+    if (!g_static_ptr[dev] || ctx != g_static_ctx[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_static_scratch);
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress");
       g_static_ptr[dev] = (double*)p;
+      g_static_ctx[dev] = ctx;
     }
     scratch = g_static_ptr[dev];
   }
@@ -1039,7 +1102,8 @@ int dev_smooth_static(cdg_handle* h, int level, const double* x, const double* b
   const bool ok = launch_smooth_first<double>(L.np, L.n, L.Dinv, b, scratch, (double*)nullptr, h->opt.omega, s) &&
                   launch_bsr<double>(3, L.np, L.n, L.hrowptr, L.hcol, L.Ahat, x, (const double*)scratch, y,
                                      h->opt.omega, nullptr, s,
-                                     (((uintptr_t)x | (uintptr_t)y) & 15) == 0 ? D.scal + S_FLAG : nullptr);
+                                     (((uintptr_t)x | (uintptr_t)y) & 15) == 0 ? D.scal + S_FLAG : nullptr,
+                                     unr_of<double>(L, 3));
   if (!ok) {
     h->err = "unsupported n_p";
     return CDG_EINVAL;
@@ -1293,8 +1357,11 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   DeviceState& D = *h->dev;
   cudaStream_t s = (cudaStream_t)stream;
   if (op == 5) {
-    launch(coarse_kernel<double, double>, (D.nc * 32 + 255) / 256, 256, s, D.nc, D.crow_seg, D.crow_off,
-           D.cinv_off, D.coarse_inv, x, y);
+    if (!x || !y) {
+      h->err = "NULL vector";
+      return CDG_EINVAL;
+    }
+    coarse_solve<double>(D, x, y, s);
     CDG_CHECK_LAUNCH(h, "coarse");
     return CDG_OK;
   }
@@ -1329,6 +1396,11 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   }
   CDG_CHECK_LAUNCH(h, "level op");
   return CDG_OK;
+}
+
+int dev_fma_probe(int blocks, long long iters, double* sink, void* stream) {
+  launch(fma64_probe_kernel, (unsigned)blocks, kThreads, (cudaStream_t)stream, iters, 0.5, sink);
+  return cudaGetLastError() == cudaSuccess ? CDG_OK : CDG_ECUDA;
 }
 
 int dev_solve_graph(const cdg_handle* h) { return h && h->dev && (h->dev->gsolve || h->dev->gm_cycle) ? 1 : 0; }

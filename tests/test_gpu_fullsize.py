@@ -8,7 +8,7 @@ compute element by element.
   sampled element is computed independently with the oracle's basis and
   quadrature for that element alone.  Checked for the 512 x 512 p = 3 FP64
   solve (7 levels, V(2,2)) and the 48^3 x 6 p = 2 solve with the FP32 V-cycle
-  (primal coarsening, V(2,2)).
+  (flux coarsening behind the p-multigrid front end, V(2,2)).
 * The 256-column solve on the 158 x 158 x 2 mesh (BF16 blocks, tensor-core
   sweeps) against single-column FP64 solves of sampled columns, and the
   64-mesh batch against single-mesh solves of sampled meshes.
@@ -76,11 +76,12 @@ def test_512_square_p3_fp64_reproduces_cubics():
 
 
 def test_48_cube_p2_fp32_vcycle_reproduces_quadratics():
-    """The 48^3 x 6 workload as bench.py runs it: primal coarsening, V(2,2), FP32 V-cycle."""
+    """The 48^3 x 6 workload as bench.py runs it: flux coarsening (Section 4.1)
+    behind the p-multigrid front end (Section 4.4), V(2,2), FP32 V-cycle."""
     from paper_2012_08024_gb300 import Solver
     mesh = kuhn_cube(48)
-    S = Solver(mesh, p=2, max_levels=6, nu_pre=2, nu_post=2, coarsen="primal", precision="fp32", tol=1e-12,
-               maxit=500).bind()
+    S = Solver(mesh, p=2, max_levels=6, nu_pre=2, nu_post=2, coarsen="flux", pmg=True, precision="fp32",
+               tol=1e-12, maxit=500).bind()
     err, it = _reproduction(mesh, S, 2, _poly3d, lambda x: np.full(x.shape[:-1], 1.4))
     print(f"48^3 p=2 FP32 V-cycle: {it} iterations, sampled projection error {err:.2e}")
     assert err <= 1e-8, err

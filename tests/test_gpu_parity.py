@@ -1,38 +1,70 @@
 """GPU parity of every step of the solve phase against the FP64 oracle, called
 through the C ABI (tree order on the device, the oracle's own numbering on the
-host).  Tolerances: single operator applies and transfers 1e-13 relative
-(FP64 summation-order differences only); one smoothing step 1e-13 plus
-4 eps max_K cond(D_K) ||omega D^-1 r|| / ||y||, because the diagonal-block
-inverses are formed by two different factorisations that agree only to
-cond(D_K) * eps (cond(D_K) reaches 1e5 under C_D = 1e4/h_avg); V-cycle 1e-9 (its dense coarsest
-solve is an explicit inverse on the device and a factorisation in the oracle,
-both exact to cond(A_n) * eps); full solves 1e-10 relative L2 with iteration
-counts within one of the oracle's."""
+host).
+
+Two references per step.  (1) The library's own host operators (exported by
+cdg_export_level, applied here in FP64 by scipy): this pins the kernels alone,
+at 1e-13 for single applies.  (2) The oracle, which builds every operator
+independently: agreement is limited by how far the two set-ups agree, `setup`
+per case.  Both sides orthonormalise monomials through the Cholesky factor of
+their Gram matrix (R2), whose condition number grows with the degree: the two
+operators agree to ~1e-15 relative for triangles at p <= 3, 2e-13 at p = 4,
+1e-11 at p = 5, 7e-11 at p = 6 and 1e-13 for tetrahedra at p = 3 (max-norm,
+measured on these meshes).
+
+Tolerances: single applies and transfers max(1e-13, setup); one smoothing step
+additionally 4 eps max_K cond(D_K) ||omega D^-1 r|| / ||y||, because the
+diagonal-block inverses are formed by two different factorisations that agree
+only to cond(D_K) eps (cond(D_K) reaches 1e5 under C_D = 1e4/h_avg); the
+coarsest solve (dense inverse plus one step of iterative refinement on the
+device, LU in numpy) cond(A_n) eps; the V-cycle 1e-9; full solves 1e-10 relative
+L2 (1e-10 + 100 setup where the two set-ups differ more) with iteration counts
+within one of the oracle's."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from synthetic import jittered_square, kuhn_cube, sin_source
 from tests.gpu_common import OracleCase, rel
 
 pytestmark = pytest.mark.gpu
 
+EPS = 2.220446049250313e-16
+
+# name: (mesh, options, setup agreement of library and oracle operators)
 CASES = {
-    "tri_p2_32": (lambda: jittered_square(32), dict(p=2, max_levels=4)),
-    "tri_p3_16_mixed_bc": (lambda: jittered_square(16, neumann_axes=(0,)), dict(p=3, max_levels=4)),
-    "tet_p2_4": (lambda: kuhn_cube(4), dict(p=2, max_levels=3)),
-    "tet_p1_5": (lambda: kuhn_cube(5, seed=2), dict(p=1, max_levels=4, seed=3)),
+    "tri_p2_32": (lambda: jittered_square(32), dict(p=2, max_levels=4), 0.0),
+    "tri_p3_16_mixed_bc": (lambda: jittered_square(16, neumann_axes=(0,)), dict(p=3, max_levels=4), 0.0),
+    "tet_p2_4": (lambda: kuhn_cube(4), dict(p=2, max_levels=3), 0.0),
+    "tet_p1_5": (lambda: kuhn_cube(5, seed=2), dict(p=1, max_levels=4, seed=3), 0.0),
+    # block sizes n_p = 15, 21, 28 (triangles, p = 4, 5, 6) and n_p = 20 (tetrahedra, p = 3)
+    "tri_p4_8": (lambda: jittered_square(8), dict(p=4, max_levels=3), 1e-12),
+    "tri_p5_6_mixed_bc": (lambda: jittered_square(6, neumann_axes=(1,)), dict(p=5, max_levels=3), 1e-10),
+    "tri_p6_6": (lambda: jittered_square(6), dict(p=6, max_levels=3), 5e-10),
+    "tet_p3_3": (lambda: kuhn_cube(3), dict(p=3, max_levels=3), 1e-13),
 }
+
+
+def exported_operator(S, level):
+    """A_l of the library's host set-up in tree order (scipy CSR) and the tree
+    order itself (perm[k] = working index of tree row k)."""
+    ex = S.export_level(level)
+    npb = S.info["np_l"][level]
+    n = len(ex["rowptr"]) - 1
+    A = sp.bsr_matrix((ex["val"], ex["col"], ex["rowptr"]), shape=(n * npb, n * npb)).tocsr()
+    return A, ex["perm"]
 
 
 @pytest.fixture(scope="module", params=list(CASES))
 def case(request):
     import torch
     from paper_2012_08024_gb300 import Solver
-    mk, kw = CASES[request.param]
+    mk, kw, setup = CASES[request.param]
     mesh = mk()
     S = Solver(mesh, **kw).bind()
     oc = OracleCase(mesh, kw["p"], kw["max_levels"], seed=kw.get("seed", 0))
     assert S.n_levels == oc.H.n_levels
+    oc.setup = setup
     return S, oc, mesh
 
 
@@ -45,19 +77,24 @@ def test_operator_apply_residual_smooth(case):
     import torch
     S, oc, _ = case
     rng = np.random.default_rng(1)
+    tol = max(1e-13, oc.setup)
     for l in range(S.n_levels):
         A = oc.H.A[l]
+        Ae, _ = exported_operator(S, l)
         n = A.shape[0]
         x = rng.standard_normal(n)
         b = rng.standard_normal(n)
-        xt, bt = _t(oc.to_tree(l, x)), _t(oc.to_tree(l, b))
+        xt_np, bt_np = oc.to_tree(l, x), oc.to_tree(l, b)
+        xt, bt = _t(xt_np), _t(bt_np)
         y = torch.empty_like(xt)
         S.apply(l, xt, y)
         torch.cuda.synchronize()
         ref = A @ x
-        assert rel(oc.to_work(l, y.cpu().numpy()), ref) <= 1e-13
+        assert rel(y.cpu().numpy(), Ae @ xt_np) <= 1e-13
+        assert rel(oc.to_work(l, y.cpu().numpy()), ref) <= tol
         S.residual(l, xt, bt, y)
-        assert rel(oc.to_work(l, y.cpu().numpy()), b - ref) <= 1e-13
+        assert rel(y.cpu().numpy(), bt_np - Ae @ xt_np) <= 1e-13
+        assert rel(oc.to_work(l, y.cpu().numpy()), b - ref) <= tol
         if l + 1 < S.n_levels:
             S.smooth(l, xt, bt, y)
             sm = oc.V.smooth(l, x, b)
@@ -66,31 +103,39 @@ def test_operator_apply_residual_smooth(case):
             Ad = A.tocsr()
             cond = max(np.linalg.cond(Ad[k * npb:(k + 1) * npb, k * npb:(k + 1) * npb].toarray())
                        for k in range(n // npb))
-            tol = 1e-13 + 4 * 2.2e-16 * cond * np.linalg.norm(corr) / np.linalg.norm(sm)
-            assert rel(oc.to_work(l, y.cpu().numpy()), sm) <= tol
+            tol_s = tol + 4 * EPS * cond * np.linalg.norm(corr) / np.linalg.norm(sm)
+            assert rel(oc.to_work(l, y.cpu().numpy()), sm) <= tol_s
 
 
 def test_restrict_prolong_coarse(case):
     import torch
     S, oc, _ = case
     rng = np.random.default_rng(2)
+    tol = max(1e-13, oc.setup)
     for l in range(S.n_levels - 1):
         L = oc.H.L[l]
         r = rng.standard_normal(L.shape[0])
         bc = torch.empty(L.shape[1], dtype=torch.float64, device="cuda")
         S.restrict(l, _t(oc.to_tree(l, r)), bc)
-        assert rel(oc.to_work(l + 1, bc.cpu().numpy()), L.T @ r) <= 1e-13
+        assert rel(oc.to_work(l + 1, bc.cpu().numpy()), L.T @ r) <= tol
         xc = rng.standard_normal(L.shape[1])
         x0 = rng.standard_normal(L.shape[0])
         xt = _t(oc.to_tree(l, x0))
         S.prolong(l, _t(oc.to_tree(l + 1, xc)), xt)
-        assert rel(oc.to_work(l, xt.cpu().numpy()), x0 + L @ xc) <= 1e-13
+        assert rel(oc.to_work(l, xt.cpu().numpy()), x0 + L @ xc) <= tol
+    # coarsest solve: against an LU solve of the library's own coarsest operator
+    # (both backward stable: they agree to cond(A_n) eps) and of the oracle's
+    Ae, _ = exported_operator(S, S.n_levels - 1)
+    Ae = Ae.toarray()
+    cond = np.linalg.cond(Ae)
+    b = rng.standard_normal(Ae.shape[0])
+    x = torch.empty(Ae.shape[0], dtype=torch.float64, device="cuda")
+    S.coarse_solve(_t(b), x)
+    assert rel(x.cpu().numpy(), np.linalg.solve(Ae, b)) <= 1e-14 + cond * EPS, (rel(x.cpu().numpy(),
+                                                                                 np.linalg.solve(Ae, b)), cond)
     Ac = oc.H.A[-1].toarray()
-    b = rng.standard_normal(Ac.shape[0])
-    x = torch.empty(Ac.shape[0], dtype=torch.float64, device="cuda")
-    S.coarse_solve(_t(oc.to_tree(S.n_levels - 1, b)), x)
-    xr = np.linalg.solve(Ac, b)
-    assert rel(oc.to_work(S.n_levels - 1, x.cpu().numpy()), xr) <= 1e-9
+    bw = oc.to_work(S.n_levels - 1, b)
+    assert rel(oc.to_work(S.n_levels - 1, x.cpu().numpy()), np.linalg.solve(Ac, bw)) <= 1e-14 + cond * max(EPS, oc.setup)
 
 
 def test_vcycle(case):
@@ -99,18 +144,15 @@ def test_vcycle(case):
     r = np.random.default_rng(3).standard_normal(oc.H.A[0].shape[0])
     z = torch.empty(len(r), dtype=torch.float64, device="cuda")
     S.vcycle(_t(oc.to_tree(0, r)), z)
-    assert rel(oc.to_work(0, z.cpu().numpy()), oc.V.apply(r)) <= 1e-9
+    assert rel(oc.to_work(0, z.cpu().numpy()), oc.V.apply(r)) <= 1e-9 + 100 * oc.setup
 
 
 def test_full_solve_matches_oracle(case):
-    """Iteration counts: within 1 of the oracle's; for solves longer than 60
-    iterations within 5% (at least 2), because the dense coarsest solves of the
-    two sides (explicit inverse on the device, LU in the oracle) agree only to
-    cond(A_n) eps ~ 1e-9 and the dot products are summed in another order: the
-    oracle's own count moves by up to 2 when its V-cycle is perturbed at that
-    level (3D cases at 65-85 iterations).
-    Solutions: at equal iteration counts within 1e-10 relative L2 of the
-    oracle's; otherwise both within 1e-10 of the direct solution."""
+    """Iteration counts within one of the oracle's.  Solutions: at equal
+    iteration counts within 1e-10 relative L2 of the oracle's iterate; otherwise
+    both within 1e-10 of the direct solution.  The GPU solution also solves the
+    library's own level-0 system (exported operator, library right-hand side)
+    to 1e-10."""
     import scipy.sparse.linalg as spl
     import torch
     from oracle.solver import pcg
@@ -121,15 +163,21 @@ def test_full_solve_matches_oracle(case):
     assert rc == 0 and hist[-1] <= 1e-10, (rc, hist[-3:])
     b = oc.L0.rhs(fq)
     uo, ho, ito = pcg(oc.H.A[0], b, oc.V.apply, tol=1e-10)
-    assert abs(it - ito) <= (1 if ito <= 60 else max(2, round(0.05 * ito))), (it, ito, hist[-3:], ho[-3:])
+    assert abs(it - ito) <= 1, (it, ito, hist[-3:], ho[-3:])
     ug = u.cpu().numpy().ravel()
+    tol = 1e-10 + 100 * oc.setup
     if it == ito:
-        assert rel(ug, uo) <= 1e-10, (it, ito, rel(ug, uo))
+        assert rel(ug, uo) <= tol, (it, ito, rel(ug, uo))
     else:
         ud = spl.spsolve(oc.H.A[0].tocsc(), b)
-        assert rel(ug, ud) <= 1e-10 and rel(uo, ud) <= 1e-10, (it, ito, rel(ug, ud), rel(uo, ud))
+        assert rel(ug, ud) <= tol and rel(uo, ud) <= 1e-10, (it, ito, rel(ug, ud), rel(uo, ud))
+    # the library's own system, in tree order
+    A0, perm = exported_operator(S, 0)
+    bl = S.rhs(_t(fq)).cpu().numpy()
+    ut = spl.spsolve(A0.tocsc(), bl[perm].ravel())
+    assert rel(u.cpu().numpy()[perm].ravel(), ut) <= 1e-10
     # the true residual of the GPU solution, by the oracle's operator
-    assert np.linalg.norm(b - oc.H.A[0] @ ug) <= 2e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(b - oc.H.A[0] @ ug) <= (2e-10 + 100 * oc.setup) * np.linalg.norm(b)
     # host-pointer path gives the same answer
     uh, hh, ith, rch = S.solve_host(fq)
     assert ith == it and rel(uh, u.cpu().numpy()) <= 1e-14
@@ -144,7 +192,7 @@ def test_rhs_matches_oracle(case):
     gD = rng.standard_normal(xbq.shape[:2])
     gN = rng.standard_normal(xbq.shape[:2])
     b = S.rhs(_t(fq), _t(gD), _t(gN))
-    assert rel(b.cpu().numpy(), oc.L0.rhs(fq, gD, gN)) <= 1e-13
+    assert rel(b.cpu().numpy(), oc.L0.rhs(fq, gD, gN)) <= max(1e-13, oc.setup)
 
 
 def test_edge_cases():
