@@ -162,11 +162,12 @@ def dist_info():
 
 def fp64_fma_peak(pkg, dev, stream):
     """FP64 FMA rate of this GPU (TFLOP/s), measured with the library's FMA probe
-    (8 independent chains per thread, 8 CTAs of 256 threads per SM), best of 5."""
+    (16 independent register-operand chains per thread, 8 CTAs of 256 threads per
+    SM), best of 5 timed launches."""
     import torch
     sink = torch.zeros(1, dtype=torch.float64, device=dev)
     blocks, iters = 152 * 8, 4096
-    fmas = blocks * 256 * 8 * iters
+    fmas = blocks * 256 * 16 * ((iters + 1) // 2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     L = pkg.lib()
     best = 0.0
@@ -240,8 +241,8 @@ def run_extras(pkg, dev, stream, barrier, only=None):
         out.update(extra_batched(pkg, dev, stream))
     if only in (None, "multi_rhs"):
         out.update(extra_multi_rhs(pkg, dev, stream))
-    if only in ("multi_rhs_bf16", "multi_rhs_bf16_cuda_cores"):   # one variant, no single solves
-        out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))
+    if only in ("multi_rhs_bf16", "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply"):
+        out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))   # one variant
     if only in (None, "adjoint"):
         out.update(extra_adjoint(pkg, dev, stream))
     if only in (None, "tet48"):
@@ -321,7 +322,8 @@ def extra_batched(pkg, dev, stream):
     return out
 
 
-def extra_multi_rhs(pkg, dev, stream, variants=("fp32", "bf16", "bf16_cuda_cores"), singles=True):
+def extra_multi_rhs(pkg, dev, stream, variants=("fp32", "fp32_tc_fp64_apply", "bf16", "bf16_tc_fp64_apply",
+                                                 "bf16_cuda_cores"), singles=True):
     import torch
     from synthetic import jittered_square, sine_combination_sources
     out = {}
@@ -337,16 +339,19 @@ def extra_multi_rhs(pkg, dev, stream, variants=("fp32", "bf16", "bf16_cuda_cores
         single.append(t)
     del S1
     # BF16 blocks: smoother sweeps on tcgen05 tensor cores (default) and on CUDA cores
-    for prec, tc, name in (("fp32", False, "fp32"), ("bf16", True, "bf16"), ("bf16", False, "bf16_cuda_cores")):
+    for prec, tc, tca, name in (("fp32", False, False, "fp32"), ("fp32", False, True, "fp32_tc_fp64_apply"),
+                                ("bf16", True, False, "bf16"), ("bf16", True, True, "bf16_tc_fp64_apply"),
+                                ("bf16", False, False, "bf16_cuda_cores")):
         if name not in variants:
             continue
         S = pkg.Solver(mesh, p=3, max_levels=5, nu_pre=2, nu_post=2, precision=prec, nrhs=R,
-                       tensor_cores=tc).bind(dev)
+                       tensor_cores=tc, tc_fp64_apply=tca).bind(dev)
         ms, (u, hists, its, rc) = _time(lambda: S.solve_multi(fq), stream, 2 if singles else 1)
         out["multi_rhs_256_" + name] = {
             "value": R * S.info["n_dofs"] / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms,
             "dofs_per_rhs": S.info["n_dofs"], "nrhs": R, "vcycle_blocks": prec,
             "smoother_sweeps": "tcgen05" if tc else "cuda cores",
+            "outer_fp64_apply": "tcgen05 exact split" if tca else "cuda cores",
             "iterations_min_max": [int(its.min()), int(its.max())], "rc": rc,
             "single_rhs_fp32_vcycle_ms": float(np.mean(single)) if single else None,
             "speedup_vs_single_solves": R * float(np.mean(single)) / ms if single else None}
@@ -441,12 +446,15 @@ def main():
                     help="skip the batched / multi-RHS / adjoint workloads")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="override the workload's V-cycle precision")
+    ap.add_argument("--fuse-transfers", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="V-cycle transfer fusion: bit 0 residual + restriction + first coarse smoothing step, "
+                         "bit 1 prolongation in the coarse level's last sweep (default 0: separate kernels)")
     ap.add_argument("--per-iteration-graphs", action="store_true",
                     help="run the CG loop as graphs per iteration half with a host read each (the same "
                          "kernels; the form a kernel profiler lists launch by launch)")
     ap.add_argument("--only-extra", default=None,
                     choices=["latency", "batched", "multi_rhs", "adjoint", "tet48", "multi_rhs_bf16",
-                             "multi_rhs_bf16_cuda_cores"],
+                             "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply"],
                     help="run one extra workload alone and print its numbers (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -478,7 +486,8 @@ def main():
     mesh = make_mesh(kind, n)
     t0 = time.perf_counter()
     S = pkg.Solver(mesh, p=p, max_levels=lv, nu_pre=nu, nu_post=nu, precision=prec, tol=1e-10, maxit=500,
-                   coarsen=coarsen, pmg=pmg, single_graph=not args.per_iteration_graphs)
+                   coarsen=coarsen, pmg=pmg, single_graph=not args.per_iteration_graphs,
+                   fuse_transfers=args.fuse_transfers)
     setup_s = time.perf_counter() - t0
     S.bind(dev)
     xq, _, _ = S.quadrature_points()

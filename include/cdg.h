@@ -122,6 +122,26 @@ typedef struct {
                                smoother sweeps on the tcgen05 tensor cores (BF16 blocks exact in
                                TF32, x split into two TF32 parts: FP32 accuracy); 0: CUDA cores.
                                A wait that reaches its limit returns CDG_ETIMEOUT. */
+  int32_t fuse_transfers;   /* bit 0: between two agglomeration levels the V-cycle computes the
+                               residual, its restriction (Section 3.4) and the coarse level's
+                               first smoothing step in one kernel; bit 1: the coarse level's
+                               last post-smoothing sweep carries the prolongation.  0 (default):
+                               separate kernels, measured faster on GB300.  The same arithmetic
+                               up to summation order. */
+  int32_t tc_fp64_apply;    /* 1: with nrhs, the FP64 level-0 apply of the outer CG runs on the
+                               tcgen05 tensor cores by exact splitting (rows of A_0 and columns
+                               of x scaled by powers of two and cut into eight 7-bit slices,
+                               BF16 slice products summed exactly in FP32 per diagonal,
+                               combined in integers and rounded once to FP64; Ozaki et al.
+                               2012); relative truncation below 2^-56 of the row and column
+                               scales.  Used where the FP32 sums provably stay exact (blocks per
+                               row x n_p x 8 x 127^2 < 2^23), else the FP64 CUDA-core apply.
+                               0 (default): the FP64 CUDA-core apply. */
+  int32_t persistent_vcycle; /* 1: each V-cycle is ONE cooperative persistent kernel whose CTAs
+                               walk the cycle's phases with grid barriers (bounded waits; an
+                               expired wait ends the solve with CDG_ETIMEOUT); used when every
+                               level has the same n_p (no p-multigrid degree steps), else the
+                               per-phase kernels.  0 (default): one kernel per phase. */
 } cdg_options;
 
 #define CDG_MAX_LEVELS 16
@@ -251,6 +271,13 @@ int cdg_solve(cdg_handle* h, const double* f_q, const double* gD_q, const double
  * residual operator and block inverses (precision 2); the outer CG is FP64. */
 int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_hist, int32_t* iters, void* stream);
 
+/* y = A_0 x for the R columns of a handle created with nrhs = R (tree order,
+ * [n_elements][n_p][R] FP64 device vectors), by the method cdg_solve_multi
+ * uses (tc_fp64_apply or the FP64 CUDA-core apply); returns when y is
+ * written.  Errors: CDG_ESTATE, CDG_ETIMEOUT (a tensor-core wait reached its
+ * limit), CDG_ECUDA. */
+int cdg_apply_multi(cdg_handle* h, const double* x, double* y, void* stream);
+
 /* Same solve from a given load vector b (device, user order, [n_elements][n_p]). */
 int cdg_solve_b(cdg_handle* h, const double* b, double* u, int32_t use_u0, double* res_hist,
                 int32_t* iters, void* stream);
@@ -321,10 +348,24 @@ int cdg_to_user(cdg_handle* h, const double* tree, double* user, void* stream);
 int cdg_smooth_static(cdg_handle* h, int32_t level, const double* x, const double* b, double* y,
                       void* stream);
 
+/* Failure injection for tests of the bounded device waits (no counterpart in
+ * the paper).  Sets the iteration limit of the waits inside kernel loops of
+ * this bound handle: the tcgen05 smoother sweep of cdg_solve_multi (precision
+ * 2 with tensor_cores), the tcgen05 FP64 apply (tc_fp64_apply) and the grid
+ * barriers of the persistent V-cycle (persistent_vcycle).  limit = 0 makes the first such wait give up at once;
+ * the kernel then sets its error flag, waits (with its default limit) for the
+ * tensor-core work it already issued, frees its tensor memory and returns, and
+ * the solve returns CDG_ETIMEOUT.  limit < 0 restores the defaults.  Nothing
+ * faults or hangs the GPU.  Holds until the next cdg_bind_device; a change
+ * drops the handle's captured solve graphs (the next solve captures them
+ * again).  Errors:
+ * CDG_EINVAL (NULL handle), CDG_ESTATE (not bound). */
+int cdg_set_wait_limit(cdg_handle* h, int32_t limit);
+
 /* FP64 FMA throughput probe (no counterpart in the paper: it measures the
  * arithmetic bound of the FP64 block-sparse kernels on the device at hand).
- * Launches blocks x 256 threads, each running 8 independent FMA chains of
- * iters steps: blocks * 256 * 8 * iters FMAs in total.  The caller times the
+ * Launches blocks x 256 threads, each running 16 independent FMA chains of
+ * ceil(iters / 2) steps: blocks * 256 * 16 * ceil(iters / 2) FMAs in total.  The caller times the
  * launch on `stream` (e.g. with CUDA events) and divides.  sink: device pointer
  * to one double that the kernel writes only for inputs that never occur (keeps
  * the chains live).  Errors: CDG_EINVAL (blocks or iters < 1, NULL sink),

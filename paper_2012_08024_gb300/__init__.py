@@ -41,7 +41,8 @@ class cdg_options(C.Structure):
                 ("tol", C.c_double), ("maxit", C.c_int32), ("nrhs", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("pmg", C.c_int32), ("autotune", C.c_int32),
                 ("beta", C.c_double), ("velocity", C.c_double * 3), ("solve_graph", C.c_int32),
-                ("tensor_cores", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("fuse_transfers", C.c_int32), ("tc_fp64_apply", C.c_int32),
+                ("persistent_vcycle", C.c_int32)]
 
 
 class cdg_info(C.Structure):
@@ -73,6 +74,8 @@ SIGNATURES = {
     "cdg_export_agglomeration": (_I32, [_P, _I32, _P]),
     "cdg_bind_device": (_I32, [_P, _P, _I64, _P]),
     "cdg_set_precision": (_I32, [_P, _I32]),
+    "cdg_set_wait_limit": (_I32, [_P, _I32]),
+    "cdg_apply_multi": (_I32, [_P, _P, _P, _P]),
     "cdg_fp64_fma_probe": (_I32, [_I32, _I64, _P, _P]),
     "cdg_rhs": (_I32, [_P, _P, _P, _P, _P, _P]),
     "cdg_solve": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P]),
@@ -163,7 +166,8 @@ class Solver:
                  coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500, nrhs: int = 0,
                  krylov: str = "cg", restart: int = 50, autotune: bool = True, pmg: bool = False,
                  beta: float = 0.0, velocity=(0.0, 0.0, 0.0), tensor_cores: bool = True,
-                 single_graph: bool = True):
+                 single_graph: bool = True, fuse_transfers: int = 0, tc_fp64_apply: bool = False,
+                 persistent_vcycle: bool = False):
         L = lib()
         self._keep = []
         self.nrhs = nrhs
@@ -186,6 +190,9 @@ class Solver:
         o.beta = beta
         o.tensor_cores = int(tensor_cores)
         o.solve_graph = int(single_graph)
+        o.fuse_transfers = int(fuse_transfers) if not isinstance(fuse_transfers, bool) else 3 * int(fuse_transfers)
+        o.tc_fp64_apply = int(tc_fp64_apply)
+        o.persistent_vcycle = int(persistent_vcycle)
         vel = list(velocity) + [0.0] * (3 - len(velocity))
         for c in range(3):
             o.velocity[c] = float(vel[c])
@@ -273,6 +280,12 @@ class Solver:
         self.info["device_bytes"] = inf.device_bytes
         return self
 
+    def set_wait_limit(self, limit: int):
+        """Failure injection (cdg_set_wait_limit): iteration limit of the bounded
+        device waits inside kernel loops; 0 = give up at once, < 0 = defaults."""
+        self._check(lib().cdg_set_wait_limit(self._h, int(limit)))
+        return self
+
     def solve_graph(self) -> bool:
         """True once a CG solve (or a GMRES restart cycle) of this handle ran as one CUDA graph launch."""
         inf = cdg_info()
@@ -343,6 +356,12 @@ class Solver:
         if rc not in (0, 3):
             self._check(rc)
         return u, hist[:it.value + 1], it.value, rc
+
+    def apply_multi(self, x, y, stream=None):
+        """y = A_0 x for the R columns (tree order, [n][n_p][R] FP64 device tensors),
+        by the method solve_multi uses (cdg_apply_multi)."""
+        n = self._sizes()[2] * self.nrhs
+        self._check(lib().cdg_apply_multi(self._h, _dvec(x, n, "x"), _dvec(y, n, "y"), _stream_ptr(stream)))
 
     def solve_multi(self, f_q, stream=None):
         """f_q [R][n_elements][nq] device -> u [R][n_elements][n_p], per-column
@@ -453,7 +472,7 @@ class BatchSolver(Solver):
     def __init__(self, meshes, p: int = 2, gamma: float = 1e4, nu_pre: int = 1, nu_post: int = 1,
                  omega: float = 2.0 / 3.0, max_levels: int = 4, seed: int = 0, precision: str = "fp64",
                  switch_kind: int = 0, coarsen: str = "flux", tol: float = 1e-10, maxit: int = 500,
-                 single_graph: bool = True):
+                 single_graph: bool = True, fuse_transfers: int = 0, persistent_vcycle: bool = False):
         L = lib()
         keep, ms = [], (cdg_mesh * len(meshes))()
         for i, mesh in enumerate(meshes):
@@ -472,6 +491,8 @@ class BatchSolver(Solver):
         o.precision, o.switch_kind = PRECISION[precision], switch_kind
         o.coarsen, o.tol, o.maxit = COARSEN[coarsen], tol, maxit
         o.solve_graph = int(single_graph)
+        o.fuse_transfers = int(fuse_transfers) if not isinstance(fuse_transfers, bool) else 3 * int(fuse_transfers)
+        o.persistent_vcycle = int(persistent_vcycle)
         h = C.c_void_p()
         rc = L.cdg_create_batched(ms, len(meshes), C.byref(o), C.byref(h))
         if rc:

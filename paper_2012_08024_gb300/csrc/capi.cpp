@@ -60,6 +60,12 @@ static int check_options(const cdg_options* opt) {
   for (int32_t flag : {opt->switch_kind, opt->coarsen, opt->autotune, opt->solve_graph, opt->tensor_cores})
     if (flag != 0 && flag != 1)
       return fail(nullptr, CDG_EINVAL, "switch_kind, coarsen, autotune, solve_graph and tensor_cores are 0 or 1");
+  if (opt->fuse_transfers < 0 || opt->fuse_transfers > 3)
+    return fail(nullptr, CDG_EINVAL, "fuse_transfers must be in [0, 3]");
+  if (opt->tc_fp64_apply != 0 && opt->tc_fp64_apply != 1)
+    return fail(nullptr, CDG_EINVAL, "tc_fp64_apply is 0 or 1");
+  if (opt->persistent_vcycle != 0 && opt->persistent_vcycle != 1)
+    return fail(nullptr, CDG_EINVAL, "persistent_vcycle is 0 or 1");
   if (opt->precision < 0 || opt->precision > 2) return fail(nullptr, CDG_EINVAL, "precision must be 0, 1 or 2");
   if (opt->nrhs < 0 || opt->nrhs > 1024) return fail(nullptr, CDG_EINVAL, "nrhs must be in [0, 1024]");
   if (opt->precision == 2 && opt->nrhs == 0)
@@ -259,6 +265,7 @@ void cdg_default_options(cdg_options* o) {
   o->autotune = 1;
   o->tensor_cores = 1;
   o->solve_graph = 1;
+  o->fuse_transfers = 0;
 }
 
 const char* cdg_last_error(const cdg_handle* h) {
@@ -474,6 +481,11 @@ int cdg_set_precision(cdg_handle* h, int32_t precision) {
   });
 }
 
+int cdg_set_wait_limit(cdg_handle* h, int32_t limit) {
+  if (!h) return CDG_EINVAL;
+  return nothrow(h, [&] { return dev_set_wait_limit(h, limit); });
+}
+
 int cdg_fp64_fma_probe(int32_t blocks, int64_t iters, double* sink, void* stream) {
   if (blocks < 1 || iters < 1 || !sink) return CDG_EINVAL;
   return dev_fma_probe(blocks, iters, sink, stream);
@@ -552,6 +564,11 @@ int cdg_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
       for (size_t r = 0; r < its.size() && h->opt.nrhs > 0; ++r) iters[r] = its[r];
     return rc;
   });
+}
+
+int cdg_apply_multi(cdg_handle* h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
+  return nothrow(h, [&] { return dev_apply_multi(h, x, y, stream); });
 }
 
 int cdg_solve_adjoint(cdg_handle* h, const double* dLdu, double* lambda, double* res_hist, int32_t* iters,

@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "device_kernels.cuh"
 #include "device_state.h"
 
 #include <atomic>
@@ -26,6 +27,9 @@ void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relax
 long long launch_count() { return g_launches.load(); }
 
 namespace {
+using cdgk::ldg;
+using cdgk::row_acc;
+using cdgk::VecLoad;
 
 // ------------------------------------------------------------------ layout
 struct Carver {
@@ -40,8 +44,37 @@ struct Carver {
   }
 };
 
+// Cuts the agglomerates of a level into consecutive chunks for the fused
+// residual + restriction: chunks close at an agglomerate boundary once they
+// hold about `target` fine rows (an agglomerate larger than that is a chunk of
+// its own).  Returns the parent boundaries; rows / parents: largest chunk.
+std::vector<int> agglomerate_chunks(const std::vector<cdg::i32>& cp, int target, int* rows, int* parents) {
+  std::vector<int> out{0};
+  *rows = *parents = 0;
+  const int nc = (int)cp.size() - 1;
+  int start = 0;
+  for (int P = 0; P < nc; ++P) {
+    const int before = cp[P] - cp[start];
+    if (P > start && before + (cp[P + 1] - cp[P]) > target) {
+      out.push_back(P);
+      *rows = std::max(*rows, before);
+      *parents = std::max(*parents, P - start);
+      start = P;
+    }
+  }
+  if (nc > start) {
+    out.push_back(nc);
+    *rows = std::max(*rows, (int)(cp[nc] - cp[start]));
+    *parents = std::max(*parents, nc - start);
+  }
+  return out;
+}
+
+// fine rows per chunk of the fused restriction: four passes of a 256-thread CTA
+inline int chunk_target(int np) { return 4 * (kThreads / 32) * (32 / np); }
+
 size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, char* base, int mr_precision,
-              int gmres_m, int maxit) {
+              int gmres_m, int maxit, int tc_fp64) {
   Carver c{base};
   const int np = H.np;
   const int nlev = (int)H.lev.size();
@@ -92,6 +125,14 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
         L.Ahat32 = c.take<float>(Sh.val.size() + 1);
       }
       L.parent = c.take<int>(L.n);
+      if (!L.ptrans && l + 1 < nlev) {
+        int rows = 0, parents = 0;
+        const std::vector<int> ch = agglomerate_chunks(H.childptr_t[l + 1], chunk_target(npl), &rows, &parents);
+        L.nchunk = (int)ch.size() - 1;
+        L.chunk_rows = rows;
+        L.chunk_parents = parents;
+        L.chunk = c.take<int>(ch.size());
+      }
     }
     if (l > 0) L.childptr = c.take<int>(L.n + 1);
     const size_t nv = (size_t)L.n * npl;
@@ -138,6 +179,8 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   D.gN_stage = c.take<double>((size_t)D.nbf * D.nfq + 1);
   D.u_stage = c.take<double>(vecbytes_elems);
   D.scal = c.take<double>((size_t)S_COUNT * D.nseg);
+  D.pv_count = c.take<unsigned>(2);
+  D.pv_err = c.take<int>(1);
   D.it_dev = c.take<int>(1);
   D.iters_dev = c.take<int>(D.nseg);
   D.hist_dev = c.take<double>((size_t)D.nseg * (maxit + 1));
@@ -153,50 +196,12 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   }
   if (nrhs > 0) {
     if (S && !S->mr) S->mr = mr_new();
-    c.off = mr_layout(H, nrhs, mr_precision, S ? S->mr : nullptr, base, c.off);
+    c.off = mr_layout(H, nrhs, mr_precision, tc_fp64, S ? S->mr : nullptr, base, c.off);
   }
   return (c.off + 255) & ~size_t(255);
 }
 
 // ------------------------------------------------------------------ kernels
-template <typename T>
-__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
-
-template <typename T, int NP>
-struct VecLoad;  // NP consecutive values of x as aligned vector loads
-template <int NP>
-struct VecLoad<float, NP> {
-  static __device__ __forceinline__ void load(const float* p, float* v) {
-    if constexpr (NP % 2 == 0) {
-#pragma unroll
-      for (int j = 0; j < NP; j += 2) {
-        const float2 t = __ldg(reinterpret_cast<const float2*>(p + j));
-        v[j] = t.x;
-        v[j + 1] = t.y;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < NP; ++j) v[j] = __ldg(p + j);
-    }
-  }
-};
-template <int NP>
-struct VecLoad<double, NP> {
-  static __device__ __forceinline__ void load(const double* p, double* v) {
-    if constexpr (NP % 2 == 0) {
-#pragma unroll
-      for (int j = 0; j < NP; j += 2) {
-        const double2 t = __ldg(reinterpret_cast<const double2*>(p + j));
-        v[j] = t.x;
-        v[j + 1] = t.y;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < NP; ++j) v[j] = __ldg(p + j);
-    }
-  }
-};
-
 // One thread per scalar row: lane = sub * NP + i handles row i of block row
 // warp * (32 / NP) + sub.  MODE 0: y = A x, 1: y = b - A x,
 // 3: y = x + omega (bh - x - Ahat x) with Ahat = D^{-1}(A - D) and bh = D^{-1} b,
@@ -220,43 +225,7 @@ __global__ void __launch_bounds__(kThreads, 8 / UNR) bsr_kernel(int n, const int
   const int i = lane - sub * NP;
   const int K = warp * RPW + sub;
   const bool active = (sub < RPW) && (K < n);
-  T acc = T(0);
-  if (active) {
-    const int b0 = rowptr[K], b1 = rowptr[K + 1];
-    if constexpr (VEC) {
-      // even n_p: the row of the block and x_J are 8-byte (FP32) / 16-byte
-      // (FP64) aligned runs, read as float2 / double2; UNR blocks per step
-      // keep UNR times the loads in flight
-      int bb = b0;
-      for (; bb + UNR <= b1; bb += UNR) {
-        T av[UNR][NP], xv[UNR][NP];
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int J = ldg(col + bb + u);
-          VecLoad<T, NP>::load(A + (size_t)(bb + u) * NP * NP + i * NP, av[u]);
-          VecLoad<T, NP>::load(x + (size_t)J * NP, xv[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < UNR; ++u)
-#pragma unroll
-          for (int j = 0; j < NP; ++j) acc = fma(av[u][j], xv[u][j], acc);
-      }
-      for (; bb < b1; ++bb) {
-        T av[NP], xv[NP];
-        VecLoad<T, NP>::load(A + (size_t)bb * NP * NP + i * NP, av);
-        VecLoad<T, NP>::load(x + (size_t)ldg(col + bb) * NP, xv);
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(av[j], xv[j], acc);
-      }
-    } else {
-      for (int bb = b0; bb < b1; ++bb) {
-        const T* a = A + (size_t)bb * NP * NP + i * NP;
-        const T* xj = x + (size_t)ldg(col + bb) * NP;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(ldg(a + j), ldg(xj + j), acc);
-      }
-    }
-  }
+  const T acc = active ? row_acc<T, NP, VEC, UNR>(K, i, rowptr, col, A, x) : T(0);
   const size_t row = (size_t)K * NP + i;
   if (MODE == 0) {
     if (active) y[row] = acc;
@@ -278,6 +247,127 @@ __global__ void __launch_bounds__(kThreads, 8 / UNR) bsr_kernel(int n, const int
   }
 }
 
+
+// Residual + restriction (Section 3.4), fused, with the first smoothing step of
+// the coarse level.  The grid is cut into chunks of whole agglomerates: CTA c
+// owns the parents [cpar[c], cpar[c+1]) of level l+1, whose children are the
+// contiguous fine rows [ccp[cpar[c]], ccp[cpar[c+1]]).
+//  1. every fine row of the chunk: r_K = b_K - A_K x (RESID; else r_K = b_K,
+//     the residual of a zero guess), then its contribution L_K^T r_K, kept in
+//     shared memory (the n_p lanes of a block row exchange r_K by shuffles);
+//  2. every parent: b_{l+1}[A] = sum of its children's contributions, in child
+//     order, written to bc;
+//  3. SMOOTH >= 1: bh_{l+1}[A] = D_A^{-1} b_{l+1}[A], and SMOOTH = 2 also
+//     x_{l+1}[A] = omega bh (the first damped block-Jacobi step from zero).
+// The residual r is never written.  Dynamic shared memory: (rows + parents) of
+// the largest chunk x NP values.
+template <typename T, int NP, bool VEC, int UNR, bool RESID, int SMOOTH>
+__global__ void __launch_bounds__(kThreads, 8 / (UNR < 2 ? 2 : UNR)) restrict_fused_kernel(
+    const int* __restrict__ cpar, const int* __restrict__ ccp, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
+    const T* __restrict__ L, T* __restrict__ bc, const T* __restrict__ Dinv_c, T* __restrict__ bh_c,
+    T* __restrict__ x_c, T omega, int max_rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_c = reinterpret_cast<T*>(smem_raw);
+  T* s_b = s_c + (size_t)max_rows * NP;
+  constexpr int RPW = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int rpp = (blockDim.x >> 5) * RPW;   // fine rows per pass of the CTA
+  const int P0 = cpar[blockIdx.x], P1 = cpar[blockIdx.x + 1];
+  const int r0 = ccp[P0], r1 = ccp[P1];
+  for (int base = 0; base < r1 - r0; base += rpp) {   // the same trip count in every thread
+    const int lr = base + (int)(threadIdx.x >> 5) * RPW + sub;
+    const int K = r0 + lr;
+    const bool active = sub < RPW && K < r1;
+    T r = T(0);
+    if (active) {
+      r = b[(size_t)K * NP + i];
+      if constexpr (RESID) r -= row_acc<T, NP, VEC, UNR>(K, i, rowptr, col, A, x);
+    }
+    const T* LK = L + (size_t)(active ? K : r0) * NP * NP + i;
+    T c = T(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const T rj = __shfl_sync(0xffffffffu, r, sub * NP + j);
+      if (active) c = fma(ldg(LK + j * NP), rj, c);
+    }
+    if (active) s_c[(size_t)lr * NP + i] = c;
+  }
+  __syncthreads();
+  const int np_ = (P1 - P0) * NP;
+  for (int t = threadIdx.x; t < np_; t += blockDim.x) {
+    const int Pl = t / NP, ii = t - Pl * NP;
+    const int P = P0 + Pl;
+    T sum = T(0);
+    for (int k = ccp[P] - r0; k < ccp[P + 1] - r0; ++k) sum += s_c[(size_t)k * NP + ii];
+    bc[(size_t)P * NP + ii] = sum;
+    if constexpr (SMOOTH > 0) s_b[t] = sum;
+  }
+  if constexpr (SMOOTH > 0) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < np_; t += blockDim.x) {
+      const int Pl = t / NP, ii = t - Pl * NP;
+      const int P = P0 + Pl;
+      const T* D = Dinv_c + (size_t)P * NP * NP + ii * NP;
+      T sum = T(0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) sum = fma(ldg(D + j), s_b[Pl * NP + j], sum);
+      bh_c[(size_t)P * NP + ii] = sum;
+      if constexpr (SMOOTH == 2) x_c[(size_t)P * NP + ii] = omega * sum;
+    }
+  }
+}
+
+// The last post-smoothing sweep of level l+1 fused with the prolongation to
+// level l (Section 3.4): y_A = x_A + omega (bh_A - x_A - (Ahat x)_A), then for
+// every child K of A: xf_K (+)= L_K y_A (ADD: the correction of a fine iterate;
+// else the fine iterate itself, after a zero pre-smoothing).  The warp's y_A
+// go to shared memory; the children of its coarse rows are one contiguous fine
+// range, whose (child, row) outputs the 32 lanes share evenly (coalesced L_K
+// rows and x_K, independent of how many children each agglomerate has).
+template <typename T, int NP, bool VEC, int UNR, bool ADD>
+__global__ void __launch_bounds__(kThreads, 8 / (UNR < 2 ? 2 : UNR)) smooth_prolong_kernel(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ col, const T* __restrict__ Ahat,
+    const T* __restrict__ x, const T* __restrict__ bh, T* __restrict__ y, T omega, const int* __restrict__ childptr,
+    const int* __restrict__ parent_f, const T* __restrict__ Lf, T* __restrict__ xf) {
+  constexpr int RPW = 32 / NP;
+  __shared__ T s_y[kThreads / 32][RPW * NP];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int sub = lane / NP;
+  const int i = lane - sub * NP;
+  const int A0 = warp * RPW;
+  const int Ag = A0 + sub;
+  const bool active = (sub < RPW) && (Ag < n);
+  if (active) {
+    const size_t row = (size_t)Ag * NP + i;
+    const T acc = row_acc<T, NP, VEC, UNR>(Ag, i, rowptr, col, Ahat, x);
+    const T xv = x[row];
+    const T yv = xv + omega * (bh[row] - xv - acc);
+    y[row] = yv;
+    s_y[wib][sub * NP + i] = yv;
+  }
+  __syncwarp();
+  if (A0 >= n) return;
+  const int A1 = min(A0 + RPW, n);
+  const int k0 = childptr[A0];
+  const int tot = (childptr[A1] - k0) * NP;
+#pragma unroll 2
+  for (int o = lane; o < tot; o += 32) {
+    const int K = k0 + o / NP;
+    const int ii = o - (K - k0) * NP;
+    const T* ya = &s_y[wib][(parent_f[K] - A0) * NP];
+    const T* LK = Lf + (size_t)K * NP * NP + ii * NP;
+    T sum = T(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) sum = fma(ldg(LK + j), ya[j], sum);
+    const size_t row = (size_t)K * NP + ii;
+    xf[row] = ADD ? xf[row] + sum : sum;
+  }
+}
 
 // bh = Dinv b; with WRITE_X also x = omega bh (first smoothing step from a zero guess)
 template <typename T, int NP, bool WRITE_X>
@@ -529,7 +619,8 @@ __global__ void hist_init_kernel(int nseg, double* __restrict__ scal) {
 // segment still open (a segment closes in the iteration it converges or breaks down), and keep the
 // loop running while a segment is open and it < maxit.
 __global__ void cg_check_kernel(cudaGraphConditionalHandle cond, int nseg, int maxit, double* __restrict__ scal,
-                                int* __restrict__ it_dev, double* __restrict__ hist, int* __restrict__ iters) {
+                                int* __restrict__ it_dev, double* __restrict__ hist, int* __restrict__ iters,
+                                const int* __restrict__ wait_err) {
   __shared__ int open;
   if (threadIdx.x == 0) open = 0;
   __syncthreads();
@@ -545,7 +636,8 @@ __global__ void cg_check_kernel(cudaGraphConditionalHandle cond, int nseg, int m
   __syncthreads();
   if (threadIdx.x == 0) {
     *it_dev = it;
-    cudaGraphSetConditional(cond, (open != 0 && it < maxit) ? 1u : 0u);
+    // a device wait that expired (persistent V-cycle) ends the loop: its output is not a V-cycle
+    cudaGraphSetConditional(cond, (open != 0 && it < maxit && *wait_err == 0) ? 1u : 0u);
   }
 }
 
@@ -676,22 +768,24 @@ __global__ void rhs_adjoint_kernel(int ne, int nq, const int* __restrict__ perm0
   out[(size_t)perm0[k] * nq + q] = s;
 }
 
-// FP64 FMA throughput probe: 8 independent dependency chains per thread, so
-// the FP64 pipe, not the FMA latency, limits the rate.  The values depend on
-// the runtime seed (nothing folds at compile time); sink is written only if
-// the chains end exactly at a value they cannot reach.
-__global__ void __launch_bounds__(kThreads) fma64_probe_kernel(long long iters, double seed, double* sink) {
-  double a[8];
+// FP64 FMA throughput probe: CHAINS independent dependency chains per thread,
+// all operands in registers (m and c arrive as arguments), so the FP64 pipe,
+// not the FMA latency, limits the rate.  The values depend on the runtime
+// arguments (nothing folds at compile time); sink is written only if the
+// chains end exactly at a value they cannot reach.
+template <int CHAINS>
+__global__ void __launch_bounds__(kThreads) fma64_probe_kernel(long long iters, double seed, double m, double c,
+                                                             double* sink) {
+  double a[CHAINS];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = seed + 1e-3 * k + 1e-9 * threadIdx.x;
-  const double m = 0.9999999, c = 1e-7;
+  for (int k = 0; k < CHAINS; ++k) a[k] = seed + 1e-3 * k + 1e-9 * threadIdx.x;
   for (long long i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    for (int k = 0; k < CHAINS; ++k) a[k] = fma(a[k], m, c);
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s += a[k];
+  for (int k = 0; k < CHAINS; ++k) s += a[k];
   if (s == -1.0) *sink = s;
 }
 
@@ -860,6 +954,90 @@ const float* opL<float>(const DevLevel& L) { return L.L32; }
 template <typename T>
 int unr_of(const DevLevel& L, int mode) { return L.unr[sizeof(T) == 8 ? 0 : 1][mode]; }
 
+// Fused residual + restriction from level l to l+1 (+ the coarse level's first
+// smoothing step, smooth: 0 none, 1 bh only, 2 bh and x = omega bh); false when
+// the level has no chunk table or needs more shared memory than a CTA has by
+// default (then the caller takes the separate kernels).
+template <typename T>
+bool launch_restrict_fused(const DeviceState& D, int l, bool resid, int smooth, const T* x, const T* b, T* bc,
+                           double omega, cudaStream_t s, double* flag) {
+  const DevLevel& F = D.lev[l];
+  const DevLevel& C = D.lev[l + 1];
+  if (!F.chunk || F.nchunk < 1) return false;
+  const size_t smem = (size_t)(F.chunk_rows + F.chunk_parents) * F.np * sizeof(T);
+  if (smem > 48 * 1024) return false;
+  const int unr = std::max(1, std::min(4, unr_of<T>(F, 1)));
+  const T* A = opA<T>(F);
+  const T* Lb = opL<T>(F);
+  const T* Dc = smooth ? opD<T>(C) : nullptr;
+  const bool vec = flag && F.np % 2 == 0;
+  bool ok = true;
+  auto go = [&](auto kern) {
+    kern<<<(unsigned)F.nchunk, kThreads, smem, s>>>(F.chunk, C.childptr, F.rowptr, F.col, A, x, b, Lb, bc, Dc,
+                                                   (T*)C.bh, (T*)C.x, (T)omega, F.chunk_rows);
+    count_launch();
+  };
+  // RESID x SMOOTH variants; VEC with 1, 2 or 4 blocks in flight for even n_p
+#define CDG_RF(NPV, VEC, UNR)                                                                                \
+  {                                                                                                          \
+    if (resid) {                                                                                             \
+      if (smooth == 2) go(restrict_fused_kernel<T, NPV, VEC, UNR, true, 2>);                                 \
+      else if (smooth == 1) go(restrict_fused_kernel<T, NPV, VEC, UNR, true, 1>);                            \
+      else go(restrict_fused_kernel<T, NPV, VEC, UNR, true, 0>);                                             \
+    } else {                                                                                                 \
+      if (smooth == 2) go(restrict_fused_kernel<T, NPV, VEC, UNR, false, 2>);                                \
+      else if (smooth == 1) go(restrict_fused_kernel<T, NPV, VEC, UNR, false, 1>);                           \
+      else go(restrict_fused_kernel<T, NPV, VEC, UNR, false, 0>);                                            \
+    }                                                                                                        \
+  }
+  auto dispatch = [&]() -> bool {
+    CDG_NP_DISPATCH(F.np, {
+      if constexpr (NP % 2 == 0) {
+        if (vec) {
+          if (unr >= 4) CDG_RF(NP, true, 4) else if (unr == 1) CDG_RF(NP, true, 1) else CDG_RF(NP, true, 2)
+        } else CDG_RF(NP, false, 1)
+      } else CDG_RF(NP, false, 1)
+    });
+    return true;
+  };
+#undef CDG_RF
+  ok = dispatch();
+  return ok;
+}
+
+// The last post-smoothing sweep of level c = l+1 fused with the prolongation to level l.
+template <typename T>
+bool launch_smooth_prolong(const DeviceState& D, int l, const T* x, const T* bh, T* y, double omega, bool add,
+                           cudaStream_t s, double* flag) {
+  const DevLevel& F = D.lev[l];
+  const DevLevel& C = D.lev[l + 1];
+  const unsigned g = rows_grid(C.n, C.np);
+  const int unr = std::max(1, std::min(4, unr_of<T>(C, 3)));
+  const bool vec = flag && C.np % 2 == 0;
+  auto go = [&](auto kern) {
+    kern<<<g, kThreads, 0, s>>>(C.n, C.hrowptr, C.hcol, opH<T>(C), x, bh, y, (T)omega, C.childptr, F.parent,
+                                opL<T>(F), (T*)F.x);
+    count_launch();
+  };
+#define CDG_SP(NPV, VEC, UNR)                                       \
+  {                                                                 \
+    if (add) go(smooth_prolong_kernel<T, NPV, VEC, UNR, true>);     \
+    else go(smooth_prolong_kernel<T, NPV, VEC, UNR, false>);        \
+  }
+  auto dispatch = [&]() -> bool {
+    CDG_NP_DISPATCH(C.np, {
+      if constexpr (NP % 2 == 0) {
+        if (vec) {
+          if (unr >= 4) CDG_SP(NP, true, 4) else if (unr == 1) CDG_SP(NP, true, 1) else CDG_SP(NP, true, 2)
+        } else CDG_SP(NP, false, 1)
+      } else CDG_SP(NP, false, 1)
+    });
+    return true;
+  };
+#undef CDG_SP
+  return dispatch();
+}
+
 // Direct solve on the coarsest level (Algorithm 3): x = A_n^{-1} b through the
 // dense inverse.  With the FP64 operator on the device (FP64 V-cycle) one step
 // of iterative refinement follows, x += A_n^{-1} (b - A_n x) with the residual
@@ -884,18 +1062,27 @@ void coarse_solve(DeviceState& D, const T* b, T* x, cudaStream_t s) {
 }
 
 // One V(nu_pre, nu_post) cycle from a zero guess (R14) on levels 0..n, with
-// b0 / z0 the level-0 right-hand side and result (precision T).
+// b0 / z0 the level-0 right-hand side and result (precision T).  With
+// fuse_transfers, between two agglomeration levels the residual, its
+// restriction and the coarse level's first smoothing step are one kernel, and
+// the coarse level's last post-smoothing sweep carries the prolongation; the
+// separate kernels remain for degree steps of the p-multigrid front end, for
+// the coarsest level and for V(nu, 0).
 template <typename T>
 bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream_t s) {
   const int nlev = D.nlev;
   const double w = o.omega;
+  double* flag = D.scal + S_FLAG;
   if (nlev == 1) {
     coarse_solve<T>(D, b0, z0, s);
     return true;
   }
+  const bool fuse = (o.fuse_transfers & 1) != 0;        // residual + restriction + first coarse step
+  const bool fuse_up = (o.fuse_transfers & 2) != 0;     // prolongation in the coarse level's last sweep
   std::vector<const T*> bl(nlev);
   bl[0] = b0;
   for (int l = 1; l < nlev; ++l) bl[l] = (const T*)D.lev[l].b;
+  std::vector<char> first_done(nlev, 0);   // the level's first smoothing step came with its right-hand side
   // downward sweep
   for (int l = 0; l + 1 < nlev; ++l) {
     DevLevel& L = D.lev[l];
@@ -904,24 +1091,37 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     T* t = (T*)L.t;
     const T* b = bl[l];
     T* bh = (T*)L.bh;
+    const bool coarse_is_last = l + 2 == nlev;
     if (o.nu_pre >= 1) {
-      if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, x, w, s)) return false;
+      if (!first_done[l] && !launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, x, w, s)) return false;
       for (int k = 1; k < o.nu_pre; ++k) {
-        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s, D.scal + S_FLAG,
+        if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, bh, t, w, nullptr, s, flag,
                            unr_of<T>(L, 3)))
           return false;
         std::swap(x, t);
       }
-      if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, D.scal + S_FLAG,
-                         unr_of<T>(L, 1)))
-        return false;
-      if (!transfer_restrict<T>(D, l, opL<T>(L), (const T*)L.r, (T*)D.lev[l + 1].b, s)) return false;
+      const int smooth = coarse_is_last ? 0 : 2;
+      if (fuse && !L.ptrans &&
+          launch_restrict_fused<T>(D, l, true, smooth, x, b, (T*)D.lev[l + 1].b, w, s, flag)) {
+        first_done[l + 1] = smooth != 0;
+      } else {
+        if (!launch_bsr<T>(1, np, L.n, L.rowptr, L.col, opA<T>(L), x, b, (T*)L.r, w, nullptr, s, flag,
+                           unr_of<T>(L, 1)))
+          return false;
+        if (!transfer_restrict<T>(D, l, opL<T>(L), (const T*)L.r, (T*)D.lev[l + 1].b, s)) return false;
+      }
       // remember which buffer holds x
       L.x = x;
       L.t = t;
     } else {
-      if (!launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, (T*)nullptr, w, s)) return false;
-      if (!transfer_restrict<T>(D, l, opL<T>(L), b, (T*)D.lev[l + 1].b, s)) return false;
+      if (!first_done[l] && !launch_smooth_first<T>(np, L.n, opD<T>(L), b, bh, (T*)nullptr, w, s)) return false;
+      const int smooth = coarse_is_last ? 0 : 1;
+      if (fuse && !L.ptrans &&
+          launch_restrict_fused<T>(D, l, false, smooth, (const T*)nullptr, b, (T*)D.lev[l + 1].b, w, s, flag)) {
+        first_done[l + 1] = smooth != 0;
+      } else if (!transfer_restrict<T>(D, l, opL<T>(L), b, (T*)D.lev[l + 1].b, s)) {
+        return false;
+      }
     }
   }
   // coarsest
@@ -930,17 +1130,26 @@ bool vcycle(DeviceState& D, const cdg_options& o, const T* b0, T* z0, cudaStream
     coarse_solve<T>(D, (const T*)C.b, (T*)C.x, s);
   }
   // upward sweep
+  std::vector<char> prolonged(nlev, 0);   // the level's correction came with the coarser level's last sweep
   for (int l = nlev - 2; l >= 0; --l) {
     DevLevel& L = D.lev[l];
     const int np = L.np;
     T* x = (T*)L.x;
     T* t = (T*)L.t;
-    if (!transfer_prolong<T>(D, l, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s)) return false;
+    if (!prolonged[l] &&
+        !transfer_prolong<T>(D, l, opL<T>(L), (const T*)D.lev[l + 1].x, x, o.nu_pre >= 1, s))
+      return false;
+    // the last sweep of this level also prolongs into level l-1 (agglomeration step)
+    const bool carry = fuse_up && l >= 1 && !D.lev[l - 1].ptrans && opL<T>(D.lev[l - 1]) != nullptr;
     for (int k = 0; k < o.nu_post; ++k) {
       T* out = (l == 0 && k + 1 == o.nu_post) ? z0 : t;
-      if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s,
-                         D.scal + S_FLAG, unr_of<T>(L, 3)))
+      if (carry && k + 1 == o.nu_post) {
+        if (!launch_smooth_prolong<T>(D, l - 1, x, (const T*)L.bh, out, w, o.nu_pre >= 1, s, flag)) return false;
+        prolonged[l - 1] = 1;
+      } else if (!launch_bsr<T>(3, np, L.n, L.hrowptr, L.hcol, opH<T>(L), x, (const T*)L.bh, out, w, nullptr, s,
+                                flag, unr_of<T>(L, 3))) {
         return false;
+      }
       if (out == t) std::swap(x, t);
       else x = out;
     }
@@ -961,11 +1170,22 @@ int precond(cdg_handle* h, const double* r, double* z, cudaStream_t s) {
   DeviceState& D = *h->dev;
   const size_t n = (size_t)D.ndofs;
   bool ok;
+  const bool pv = h->opt.persistent_vcycle != 0 && !D.pv_failed;
   if (D.precision == 0) {
-    ok = vcycle<double>(D, h->opt, r, z, s);
+    ok = pv && vcycle_persistent(D, h->opt, false, r, z, D.pv_count, D.pv_err, s);
+    if (!ok) {
+      if (pv) cudaGetLastError();   // a refused cooperative launch: take the per-phase kernels
+      D.pv_failed = D.pv_failed || pv;
+      ok = vcycle<double>(D, h->opt, r, z, s);
+    }
   } else {
     launch(convert_kernel<double, float>, vec_grid(n), kThreads, s, n, r, D.r32);
-    ok = vcycle<float>(D, h->opt, D.r32, D.z32, s);
+    ok = pv && vcycle_persistent(D, h->opt, true, D.r32, D.z32, D.pv_count, D.pv_err, s);
+    if (!ok) {
+      if (pv) cudaGetLastError();
+      D.pv_failed = D.pv_failed || pv;
+      ok = vcycle<float>(D, h->opt, D.r32, D.z32, s);
+    }
     launch(convert_kernel<float, double>, vec_grid(n), kThreads, s, n, D.z32, z);
   }
   if (!ok) {
@@ -1116,7 +1336,7 @@ static int gmres_len(const cdg_options& o) { return o.krylov == 1 ? o.restart : 
 
 int dev_bytes(const cdg_handle* h, int64_t* bytes) {
   *bytes = (int64_t)layout(h->H, h->opt.precision == 2 ? 1 : h->opt.precision, h->opt.nrhs, nullptr, nullptr,
-                          h->opt.precision, gmres_len(h->opt), h->opt.maxit);
+                          h->opt.precision, gmres_len(h->opt), h->opt.maxit, h->opt.tc_fp64_apply);
   return CDG_OK;
 }
 
@@ -1237,7 +1457,8 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   const cdg::Hierarchy& H = h->H;
   const int prec = h->opt.precision == 2 ? 1 : h->opt.precision;
   const int64_t need =
-      (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision, gmres_len(h->opt), h->opt.maxit);
+      (int64_t)layout(H, prec, h->opt.nrhs, nullptr, nullptr, h->opt.precision, gmres_len(h->opt), h->opt.maxit,
+                      h->opt.tc_fp64_apply);
   if (bytes < need) {
     h->err = "device buffer too small: need " + std::to_string(need) + " bytes";
     return CDG_ENOMEM;
@@ -1251,7 +1472,8 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
   DeviceState& D = *h->dev;
   D.base = (char*)buf;
   D.bytes = bytes;
-  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision, gmres_len(h->opt), h->opt.maxit);
+  layout(H, prec, h->opt.nrhs, &D, (char*)buf, h->opt.precision, gmres_len(h->opt), h->opt.maxit,
+         h->opt.tc_fp64_apply);
   D.precision = h->opt.precision == 2 ? 1 : h->opt.precision;
   cudaStream_t s = (cudaStream_t)stream;
   const int nlev = D.nlev;
@@ -1275,6 +1497,10 @@ int dev_bind(cdg_handle* h, void* buf, int64_t bytes, void* stream) {
       if (L.Ahat32) upload(L.Ahat32, to_f32(Sh.val), s);
     }
     if (l > 0) upload(L.childptr, H.childptr_t[l], s);
+    if (L.chunk) {
+      int rows = 0, parents = 0;
+      upload(L.chunk, agglomerate_chunks(H.childptr_t[l + 1], chunk_target(L.np), &rows, &parents), s);
+    }
     // every synchronous upload above finishes before the host vectors die
     cudaStreamSynchronize(s);
   }
@@ -1398,8 +1624,30 @@ int dev_level_op(cdg_handle* h, int op, int level, const double* x, const double
   return CDG_OK;
 }
 
+int dev_set_wait_limit(cdg_handle* h, int limit) {
+  if (!h->dev) {
+    h->err = "cdg_bind_device has not been called";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  const int v = limit < 0 ? -1 : limit;
+  if (v != D.wait_limit) {
+    // captured graphs hold the limit as a kernel argument: capture again at the next solve
+    cudaStreamSynchronize(D.stream);
+    if (D.g1) cudaGraphExecDestroy(D.g1);
+    if (D.g2) cudaGraphExecDestroy(D.g2);
+    if (D.gsolve) cudaGraphExecDestroy(D.gsolve);
+    D.g1 = D.g2 = D.gsolve = nullptr;
+    gmres_release(D);
+  }
+  D.wait_limit = v;
+  return CDG_OK;
+}
+
 int dev_fma_probe(int blocks, long long iters, double* sink, void* stream) {
-  launch(fma64_probe_kernel, (unsigned)blocks, kThreads, (cudaStream_t)stream, iters, 0.5, sink);
+  // 16 chains of iters / 2 steps: the same FMA count as 8 chains of iters steps
+  launch(fma64_probe_kernel<16>, (unsigned)blocks, kThreads, (cudaStream_t)stream, (iters + 1) / 2, 0.5,
+         0.9999999, 1e-7, sink);
   return cudaGetLastError() == cudaSuccess ? CDG_OK : CDG_ECUDA;
 }
 
@@ -1534,7 +1782,7 @@ static int capture_solve(cdg_handle* h) {
   int rc = cg_part1(h, D.stream);
   if (rc == CDG_OK) {
     launch(cg_check_kernel, 1u, 64u, D.stream, cond, D.nseg, h->opt.maxit, D.scal, D.it_dev, D.hist_dev,
-           D.iters_dev);
+           D.iters_dev, (const int*)D.pv_err);
     rc = cg_part2(h, D.stream);
   }
   cudaGraph_t captured = nullptr;
@@ -1583,6 +1831,7 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
     u_dev = D.u_stage;
   }
   cudaMemsetAsync(D.scal, 0, sizeof(double) * S_COUNT * nseg, s);   // scalars and the wait-timeout flag
+  cudaMemsetAsync(D.pv_err, 0, sizeof(int), s);
   // right-hand side in tree order
   if (b_user) {
     launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, b_user, D.bt, 1);
@@ -1712,9 +1961,15 @@ int dev_solve(cdg_handle* h, const double* f_q, const double* gD, const double* 
   }
   launch(permute_kernel, vec_grid(n), kThreads, s, (int)D.ne, D.np, D.perm0, D.x, u_dev, 0);
   if (host_ptrs) cudaMemcpyAsync(u, D.u_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  int pv_err = 0;
+  cudaMemcpyAsync(&pv_err, D.pv_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve end");
   CDG_CHECK_LAUNCH(h, "solve end");
+  if (pv_err) {
+    h->err = "a grid barrier of the persistent V-cycle reached its iteration limit";
+    return CDG_ETIMEOUT;
+  }
   if (status == CDG_ENOCONV) {
     for (int m = 0; m < nseg; ++m)
       if (!done[m]) iters[m] = it;

@@ -322,6 +322,13 @@ struct MR {
   bool tuned = false;
   bool tc = false;             // smoother sweeps on tcgen05 (BF16 blocks)
   int* tc_err = nullptr;       // set by a tensor-core kernel whose wait timed out
+  // FP64 level-0 apply on tcgen05 by exact splitting: B operand images of the
+  // slices of A_0, row exponents, slices of x and column exponents (device_ozaki.cu)
+  bool oz = false;
+  void* oz_img = nullptr;
+  int* oz_eA = nullptr;
+  void* oz_xs = nullptr;
+  int* oz_maxb = nullptr;
 };
 
 void mr_tuning(const MR& M, int level, int nlev, int32_t* out) {
@@ -367,7 +374,7 @@ MR* mr_new() { return new MR(); }
 void mr_delete(MR* m) { delete m; }
 
 // Carves the multi-column buffers after `off`; returns the new end offset.
-size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off) {
+size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, int tc_fp64, MR* mr, char* base, size_t off) {
   MRCarver c{base, off};
   MR tmp;
   MR& M = mr ? *mr : tmp;
@@ -410,6 +417,13 @@ size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* ba
   M.scal = c.take<double>((size_t)R * S_COUNT);
   M.partial = c.take<double>((size_t)2 * M.G * R);
   M.tc_err = c.take<int>(1);
+  M.oz = tc_fp64 != 0 && oz_feasible(H.A_t[0], np);
+  if (M.oz) {
+    M.oz_img = c.take<char>(oz_image_bytes(H.A_t[0]));
+    M.oz_eA = c.take<int>((size_t)H.lev[0].n * 16);
+    M.oz_xs = c.take<char>(oz_xslice_bytes(H.lev[0].n, np, R));
+    M.oz_maxb = c.take<int>(R);
+  }
   return c.off;
 }
 
@@ -427,6 +441,17 @@ void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s) {
       up(L.Ahat, H.Ahat_t[l].val);
       upload_conv<float>(L.Dinv, H.Dinv_t[l], s);
       up(L.L, H.L_t[l]);
+    }
+  }
+  if (M.oz) {
+    std::vector<uint16_t> img;
+    std::vector<int32_t> eA;
+    if (oz_prepare(H.A_t[0], H.np, img, eA)) {
+      cudaMemcpyAsync(M.oz_img, img.data(), sizeof(uint16_t) * img.size(), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(M.oz_eA, eA.data(), sizeof(int32_t) * eA.size(), cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+    } else {
+      M.oz = false;
     }
   }
 }
@@ -477,7 +502,7 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
                  float* y) -> bool {
     const int n = D.lev[l].n;
     if (mode == 3 && M.tc)
-      return mr_tc_smooth(np, n, R, rp, cl, A, x, b, y, w, M.tc_err, s);
+      return mr_tc_smooth(np, n, R, rp, cl, A, x, b, y, w, M.tc_err, D.wait_limit, s);
     const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode);
     MR_NP_DISPATCH(np, {
       if (mode == 1)
@@ -555,6 +580,9 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
 
 bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t s) {
   const DevLevel& L0 = D.lev[0];
+  if (M.oz)
+    return oz_apply(D.np, L0.n, M.R, L0.rowptr, L0.col, M.oz_img, M.oz_eA, M.oz_xs, M.oz_maxb, x, y, M.tc_err,
+                    D.wait_limit, s);
   const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0);
   MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, L0.n, M.R, L0.rowptr, L0.col, L0.A, x,
                                                                      (const double*)nullptr, y, 0.0, s)));
@@ -666,7 +694,7 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   }
   cudaMemsetAsync(M.scal, 0, sizeof(double) * (size_t)R * S_COUNT, s);
   M.tc = M.bf16 && o.tensor_cores != 0 && D.np <= 16;
-  if (M.tc) cudaMemsetAsync(M.tc_err, 0, sizeof(int), s);
+  if (M.tc || M.oz) cudaMemsetAsync(M.tc_err, 0, sizeof(int), s);
   MR_NP_DISPATCH(D.np, mr_rhs_kernel<NP><<<(unsigned)D.ne, T, 0, s>>>(R, D.nq, (int)D.ne, D.perm0, D.rhs_vol, f_q, M.bt));
   count_launch();
   cudaMemsetAsync(M.x, 0, sizeof(double) * nv, s);
@@ -719,11 +747,14 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
       count_launch();
       mr_dot(D, M, M.r, M.r, nullptr, 1, o.tol, s);
       cudaMemcpyAsync(hs.data(), M.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
+      int tc_err_it = 0;
+      if (M.tc || M.oz) cudaMemcpyAsync(&tc_err_it, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
         h->err = std::string("solve_multi: ") + cudaGetErrorString(e);
         return CDG_ECUDA;
       }
+      if (tc_err_it) break;   // a sweep gave up: its rows are not smoothed; reported below
       ++it;
       for (int r = 0; r < R; ++r) {
         if (done[r]) continue;
@@ -754,7 +785,7 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   mr_out_kernel<<<(unsigned)D.ne, T, 0, s>>>(R, D.np, D.perm0, M.x, (int)D.ne, u);
   count_launch();
   int tc_err = 0;
-  if (M.tc) cudaMemcpyAsync(&tc_err, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (M.tc || M.oz) cudaMemcpyAsync(&tc_err, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -762,9 +793,39 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
     return CDG_ECUDA;
   }
   if (tc_err) {
-    h->err = "solve_multi: a tensor-core smoother wait reached its iteration limit";
+    h->err = "solve_multi: a tensor-core wait reached its iteration limit";
     return CDG_ETIMEOUT;
   }
   if (status == CDG_ENOCONV) h->err = "maximum number of iterations reached";
   return status;
+}
+
+// y = A_0 x for the R columns of a multi-right-hand-side handle (tree order,
+// [n][n_p][R] FP64, device), by the method its solves use; synchronous.
+int dev_apply_multi(cdg_handle* h, const double* x, double* y, void* stream) {
+  if (!h->dev || !h->dev->mr) {
+    h->err = "cdg_apply_multi needs a handle created with nrhs > 0 and bound to a device buffer";
+    return CDG_ESTATE;
+  }
+  DeviceState& D = *h->dev;
+  MR& M = *D.mr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (M.oz) cudaMemsetAsync(M.tc_err, 0, sizeof(int), s);
+  if (!mr_apply64(D, M, x, y, s)) {
+    h->err = "unsupported n_p for cdg_apply_multi";
+    return CDG_EINVAL;
+  }
+  int err = 0;
+  if (M.oz) cudaMemcpyAsync(&err, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    h->err = std::string("cdg_apply_multi: ") + cudaGetErrorString(e);
+    return CDG_ECUDA;
+  }
+  if (err) {
+    h->err = "cdg_apply_multi: a tensor-core wait reached its iteration limit";
+    return CDG_ETIMEOUT;
+  }
+  return CDG_OK;
 }

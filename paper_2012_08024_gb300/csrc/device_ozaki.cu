@@ -1,0 +1,364 @@
+// FP64 level-0 apply of the many-right-hand-side CG, Y = A_0 X for R columns,
+// on the tcgen05 tensor cores by exact splitting (Ozaki, Ogita, Oishi and Rump,
+// "Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", 2012).
+//
+// Every row (K, i) of A_0 is scaled by a power of two 2^{E_A(K,i)} above its
+// largest entry and every column r of X by 2^{E_X(r)}; the scaled values, in
+// (-1, 1), are cut into S = 8 signed 7-bit integer slices,
+//   a = 2^{E_A} sum_s a_s 2^{-7(s+1)},   x = 2^{E_X} sum_t x_t 2^{-7(t+1)},
+// each exact in BF16.  A BF16 x BF16 product is exact in FP32, and so is a sum
+// of them while it stays an integer below 2^24 (checked on the host, with one
+// bit of headroom: blocks per row x n_p x S x 127^2 < 2^23).  The slice products of one diagonal d = s + t share the
+// scale 2^{-7(d+2)}, so they go to one FP32 accumulator: the MMA of slice t of
+// X against the stacked slices [A_0; ...; A_{S-1-t}] (N = 16 (S - t) rows)
+// writes at TMEM column 16 t, i.e. onto the accumulators d = t .. S-1.  The
+// pairs s + t >= S are left out (relative truncation below 2^-56 of the row
+// and column scales).  The epilogue converts the eight integer-valued
+// accumulators to integers, combines them exactly in 64-bit integers and
+// rounds once to FP64.
+//
+// Layout: the slices of one block are stored as the 4 KB shared-memory image
+// of the MMA B operand (128 rows s * 16 + i, K = 16 columns j, canonical
+// K-major SWIZZLE_NONE core matrices: 8 rows x 16 bytes, LBO = 128 bytes
+// along K, SBO = 256 bytes between 8-row groups); X is sliced once per apply
+// into [n][S][n_p][R] BF16 and staged per block as S operands A = X_J^T
+// (128 columns x 16, same layout).  One CTA of 128 threads owns a tile of 128
+// columns; one thread issues the MMAs of a block and commits them to the
+// mbarrier of its shared-memory stage (two stages, so staging the next block
+// overlaps the MMAs of the current one).  Every wait has an iteration limit;
+// on expiry the kernel sets the error flag, drains its MMAs (default limit),
+// frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "device_state.h"
+#include "host_setup.h"
+
+namespace {
+
+constexpr int kS = 8;                         // slices per operand
+constexpr int kTile = 128;                    // columns per tile (MMA M, TMEM lanes)
+constexpr int kBRows = 16 * kS;               // B operand rows: slice s, row i
+constexpr uint32_t kLBO = 128, kSBO = 256;    // bytes (BF16, K = 16)
+constexpr int kXBytes = kTile * 16 * 2;       // one X slice operand: 4 KB
+constexpr int kABytes = kBRows * 16 * 2;      // all A slices of one block: 4 KB
+constexpr int kStageBytes = kS * kXBytes + kABytes;
+constexpr int kStages = 2;
+constexpr int kWaitLimit = 1 << 22;
+constexpr int kTmemCols = 16 * kS;            // accumulators d = 0 .. S-1, 16 columns each
+
+__host__ __device__ __forceinline__ int kmaj16(int row, int k) {
+  return (row >> 3) * (int)kSBO + (k >> 3) * (int)kLBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(kLBO >> 4) << 16;
+  d |= (uint64_t)(kSBO >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of the tcgen05 family; base offset 0, no swizzle
+  return d;
+}
+
+// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N rows of B, M = 128
+__device__ __forceinline__ uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, int limit) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+  return done != 0;
+}
+
+// BF16 bits of a signed integer |k| <= 127 (exact): 2^23 + k as FP32 bits minus 2^23
+__device__ __forceinline__ uint32_t bf16_small(uint32_t mag, bool neg) {
+  const float f = __uint_as_float(0x4B000000u | mag) - 8388608.0f;
+  return ((__float_as_uint(f) >> 16) & 0x7FFFu) | (neg ? 0x8000u : 0u);
+}
+
+// 2^k * v for an integer |v| < 2^53, built from its bits (exact); ldexp outside the normal range
+__device__ __forceinline__ double i64_scaled(long long v, int k) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int e = 63 - __clzll((long long)a);
+  const int be = e + 1023 + k;
+  if (be <= 0 || be >= 2047) return ldexp((double)v, k);
+  const unsigned long long mant = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | mant));
+}
+
+// per column r: the largest biased FP64 exponent of x[.][r] (0 for a zero column)
+__global__ void oz_colexp_kernel(size_t nrows, int R, const double* __restrict__ x, int* __restrict__ maxb) {
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const size_t lo = nrows * blockIdx.x / gridDim.x, hi = nrows * (blockIdx.x + 1) / gridDim.x;
+  int m = 0;
+  for (size_t row = lo; row < hi; ++row) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[row * R + r]);
+    m = max(m, (int)((b >> 52) & 0x7FF));
+  }
+  atomicMax(maxb + r, m);
+}
+
+// xs[K][t][j][r] = slice t of x[K][j][r] (BF16 bits), the column scaled by 2^{-(maxb - 1022)}
+__global__ void oz_slice_kernel(size_t nrows, int np, int R, const double* __restrict__ x,
+                                const int* __restrict__ maxb, uint16_t* __restrict__ xs) {
+  const size_t tot = nrows * R;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = t / R;
+    const int r = (int)(t - row * R);
+    const size_t K = row / np;
+    const int j = (int)(row - K * np);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x[t]);
+    const bool neg = (bits >> 63) != 0;
+    const int b = (int)((bits >> 52) & 0x7FF);
+    unsigned long long F = 0;   // |x| 2^{56 - E_X}, truncated: < 2^56
+    if (b != 0) {
+      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = b - maxb[r] + 3;   // <= 3
+      if (sh >= 0) F = M << sh;
+      else if (sh > -64) F = M >> (-sh);
+    }
+    uint16_t* o = xs + (K * kS * np + j) * (size_t)R + r;
+#pragma unroll
+    for (int s = 0; s < kS; ++s)
+      o[(size_t)s * np * R] = (uint16_t)bf16_small((uint32_t)((F >> (49 - 7 * s)) & 127u), neg);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, const int* __restrict__ rowptr,
+                                                         const int* __restrict__ col,
+                                                         const uint16_t* __restrict__ Asl,
+                                                         const int* __restrict__ eA, const uint16_t* __restrict__ xs,
+                                                         const int* __restrict__ maxb, double* __restrict__ y,
+                                                         int* __restrict__ err, int wait_limit) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = blockIdx.y * kTile + tid;   // this thread's column
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "n"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int ex = r < R ? maxb[r] - 1022 : 0;   // E_X of this column
+  uint32_t phase[kStages] = {0u, 0u};
+  bool busy[kStages] = {false, false};
+  int g = 0;
+  bool ok = true;
+  for (int K = blockIdx.x; K < n && ok; K += gridDim.x) {
+    const int b0 = rowptr[K], b1 = rowptr[K + 1];
+    for (int bb = b0; bb < b1 && ok; ++bb, ++g) {
+      const int st = g & 1;
+      if (busy[st]) {   // the MMAs that last read this stage
+        ok = __syncthreads_and(wait_phase(smem_u32(&bar[st]), phase[st], wait_limit) ? 1 : 0) != 0;
+        phase[st] ^= 1u;
+        busy[st] = false;
+        if (!ok) break;
+      }
+      unsigned char* sx = smem + st * kStageBytes;
+      unsigned char* sa = sx + kS * kXBytes;
+      const int J = col[bb];
+      // X_J^T slices: row = this column, K = j (zero beyond n_p and beyond R)
+#pragma unroll
+      for (int t = 0; t < kS; ++t) {
+        uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (r < R) {
+          const uint16_t* src = xs + ((size_t)J * kS * NP + (size_t)t * NP) * R + r;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) w[j >> 1] |= (uint32_t)src[(size_t)j * R] << ((j & 1) * 16);
+        }
+        unsigned char* dst = sx + t * kXBytes;
+        *reinterpret_cast<uint4*>(dst + kmaj16(tid, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(dst + kmaj16(tid, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      // the block's B operand image (4 KB)
+      const uint4* ai = reinterpret_cast<const uint4*>(Asl + (size_t)bb * (kABytes / 2));
+      reinterpret_cast<uint4*>(sa)[tid] = __ldg(ai + tid);
+      reinterpret_cast<uint4*>(sa)[tid + kTile] = __ldg(ai + tid + kTile);
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint64_t bdesc = smem_desc(smem_u32(sa));
+#pragma unroll
+        for (int t = 0; t < kS; ++t)
+          mma_bf16(tmem + (uint32_t)(16 * t), smem_desc(smem_u32(sx + t * kXBytes)), bdesc, idesc_bf16(16 * (kS - t)),
+                   (bb > b0 || t > 0) ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar[st])));
+      }
+      busy[st] = true;
+    }
+    // the row's MMAs complete
+    for (int st = 0; st < kStages && ok; ++st) {
+      if (!busy[st]) continue;
+      ok = __syncthreads_and(wait_phase(smem_u32(&bar[st]), phase[st], wait_limit) ? 1 : 0) != 0;
+      phase[st] ^= 1u;
+      busy[st] = false;
+    }
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: y[K][i][r] = 2^{E_A + E_X - 63} sum_d acc_d 2^{7 (S - 1 - d)}, in two halves of i
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int h = 0; h < (NP + 7) / 8; ++h) {
+      uint32_t v[kS][8];
+#pragma unroll
+      for (int d = 0; d < kS; ++d)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                       "=r"(v[d][6]), "=r"(v[d][7])
+                     : "r"(taddr + (uint32_t)(16 * d + 8 * h)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (r < R) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = 8 * h + q;
+          if (i >= NP) break;
+          int a[kS];
+#pragma unroll
+          for (int d = 0; d < kS; ++d) a[d] = b1 > b0 ? __float2int_rz(__uint_as_float(v[d][q])) : 0;
+          const int p0 = a[0] * 128 + a[1], p1 = a[2] * 128 + a[3];
+          const int p2 = a[4] * 128 + a[5], p3 = a[6] * 128 + a[7];
+          const long long vh = (long long)p0 * 16384 + p1, vl = (long long)p2 * 16384 + p3;
+          const int k = eA[(size_t)K * 16 + i] + ex - 63;
+          y[((size_t)K * NP + i) * R + r] = i64_scaled(vh, k + 28) + i64_scaled(vl, k);
+        }
+      }
+    }
+    // the next row's MMAs overwrite the accumulators: every lane has read them
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    for (int st = 0; st < kStages; ++st)   // MMAs still running on a stage
+      if (busy[st]) wait_phase(smem_u32(&bar[st]), phase[st], kWaitLimit);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols));
+}
+
+// S signed 7-bit slices of a, scaled by 2^{-E} (|a| < 2^E): a = 2^E sum_s out[s] 2^{-7(s+1)} + rest
+void host_slices(double a, int E, int out[kS]) {
+  const double v = std::ldexp(std::fabs(a), 56 - E);   // < 2^56, exact
+  const uint64_t F = (uint64_t)v;                      // floor
+  const int sg = a < 0 ? -1 : 1;
+  for (int s = 0; s < kS; ++s) out[s] = sg * (int)((F >> (49 - 7 * s)) & 127u);
+}
+
+uint16_t host_bf16_int(int k) {
+  const float f = (float)k;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (uint16_t)(u >> 16);
+}
+
+}  // namespace
+
+size_t oz_image_bytes(const cdg::BSR& A) { return (size_t)A.nnzb() * kABytes; }
+size_t oz_xslice_bytes(int64_t n, int np, int R) { return (size_t)n * kS * np * R * sizeof(uint16_t); }
+int oz_smem_bytes() { return kStages * kStageBytes; }
+
+// The split is exact when every FP32 accumulator stays an integer below 2^23
+// (below 2^24 for exact FP32 sums, one bit more of headroom for the int32
+// combination of the epilogue): blocks per row x n_p x S pairs x 127^2 < 2^23.
+bool oz_feasible(const cdg::BSR& A, int np) {
+  if (np > 16) return false;
+  int64_t maxblk = 0;
+  for (int64_t K = 0; K < A.nrows; ++K) maxblk = std::max<int64_t>(maxblk, A.rowptr[K + 1] - A.rowptr[K]);
+  return (double)maxblk * np * kS * 127.0 * 127.0 < 8388608.0;
+}
+
+// Host preparation of the slices of A_0: the B operand image of every block and
+// the row exponents eA[K * 16 + i].  False when the split would not be exact.
+bool oz_prepare(const cdg::BSR& A, int np, std::vector<uint16_t>& img, std::vector<int32_t>& eA) {
+  if (!oz_feasible(A, np)) return false;
+  const int64_t n = A.nrows;
+  img.assign((size_t)A.nnzb() * (kABytes / 2), 0);
+  eA.assign((size_t)n * 16, 0);
+  for (int64_t K = 0; K < n; ++K) {
+    for (int i = 0; i < np; ++i) {
+      double m = 0.0;
+      for (int64_t b = A.rowptr[K]; b < A.rowptr[K + 1]; ++b)
+        for (int j = 0; j < np; ++j) m = std::max(m, std::fabs(A.block(b)[i * np + j]));
+      int e = 0;
+      if (m > 0.0) std::frexp(m, &e);   // m < 2^e
+      eA[(size_t)K * 16 + i] = e;
+    }
+    for (int64_t b = A.rowptr[K]; b < A.rowptr[K + 1]; ++b) {
+      uint16_t* o = img.data() + (size_t)b * (kABytes / 2);
+      for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) {
+          int sl[kS];
+          host_slices(A.block(b)[i * np + j], eA[(size_t)K * 16 + i], sl);
+          for (int s = 0; s < kS; ++s) o[kmaj16(s * 16 + i, j) / 2] = host_bf16_int(sl[s]);
+        }
+    }
+  }
+  return true;
+}
+
+// y = A_0 x for R columns ([n][np][R] FP64 vectors): column exponents, slices of x, tensor-core products.
+bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const void* img, const int* eA, void* xs,
+              int* maxb, const double* x, double* y, int* err, int wait_limit, cudaStream_t s) {
+  const size_t nrows = (size_t)n * np;
+  cudaMemsetAsync(maxb, 0, sizeof(int) * R, s);
+  const unsigned ty = (unsigned)((R + 255) / 256);
+  oz_colexp_kernel<<<dim3(2 * 152, ty), 256, 0, s>>>(nrows, R, x, maxb);
+  oz_slice_kernel<<<4 * 152 * 4, 256, 0, s>>>(nrows, np, R, x, maxb, (uint16_t*)xs);
+  const int lim = wait_limit < 0 ? kWaitLimit : std::min(wait_limit, kWaitLimit);
+  // three CTAs per SM (72 KB of shared memory, 128 TMEM columns each): the whole grid is resident
+  const unsigned tiles = (unsigned)((R + kTile - 1) / kTile);
+  const dim3 grid((unsigned)std::max(1, std::min(n, (int)(152 * 3 / tiles))), tiles);
+  const int smem = oz_smem_bytes();
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kern<<<grid, kTile, smem, s>>>(n, R, rowptr, col, (const uint16_t*)img, eA, (const uint16_t*)xs, maxb, y, err,
+                                   lim);
+  };
+  switch (np) {
+    case 3: go(oz_apply_kernel<3>); break;
+    case 4: go(oz_apply_kernel<4>); break;
+    case 6: go(oz_apply_kernel<6>); break;
+    case 10: go(oz_apply_kernel<10>); break;
+    default: return false;
+  }
+  count_launch(3);
+  return true;
+}

@@ -28,6 +28,10 @@ struct DevLevel {
   double* L = nullptr;
   int* parent = nullptr;
   int* childptr = nullptr;   // children range of each element of this level (l >= 1)
+  // chunks of whole agglomerates of level l+1 for the fused residual + restriction
+  // (one CTA each): parent boundaries [nchunk+1]; rows / parents of the largest chunk
+  int* chunk = nullptr;
+  int nchunk = 0, chunk_rows = 0, chunk_parents = 0;
   float* A32 = nullptr;
   float* Dinv32 = nullptr;
   float* L32 = nullptr;
@@ -90,6 +94,14 @@ struct DeviceState {
   cudaEvent_t ev_in = nullptr;
   cudaGraphExec_t g1 = nullptr, g2 = nullptr;
   long long g1_kernels = 0, g2_kernels = 0;
+  // iteration limit of the bounded device waits inside kernel loops (< 0: each kernel's
+  // default); set by cdg_set_wait_limit to exercise the timeout path
+  int wait_limit = -1;
+  // persistent V-cycle (device_persist.cu): grid-barrier words, its error flag, and
+  // whether it was refused (e.g. a cooperative launch inside a graph capture)
+  unsigned* pv_count = nullptr;
+  int* pv_err = nullptr;
+  bool pv_failed = false;
   // the whole CG solve as one graph: a conditional WHILE node around [G1, check, G2];
   // the check kernel records the residual histories and ends the loop on the device
   cudaGraphExec_t gsolve = nullptr;
@@ -170,11 +182,28 @@ void gmres_release(DeviceState& D);
 namespace cdg { struct Hierarchy; }
 MR* mr_new();
 void mr_delete(MR* m);
-size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, MR* mr, char* base, size_t off);
+// tc_fp64: the FP64 level-0 apply of the outer CG on tcgen05 by exact splitting (device_ozaki.cu)
+size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, int tc_fp64, MR* mr, char* base, size_t off);
 void mr_upload(const cdg::Hierarchy& H, MR& M, cudaStream_t s);
+int dev_apply_multi(cdg_handle* h, const double* x, double* y, void* stream);
+
+// device_persist.cu: one V-cycle as one cooperative persistent launch (false: not applicable
+// to this hierarchy, or the launch was refused)
+bool vcycle_persistent(DeviceState& D, const cdg_options& o, bool fp32, const void* b0, void* z0, unsigned* count,
+                       int* err, cudaStream_t s);
+
+// device_ozaki.cu
+namespace cdg { struct BSR; }
+size_t oz_image_bytes(const cdg::BSR& A);
+size_t oz_xslice_bytes(int64_t n, int np, int R);
+bool oz_feasible(const cdg::BSR& A, int np);
+bool oz_prepare(const cdg::BSR& A, int np, std::vector<uint16_t>& img, std::vector<int32_t>& eA);
+bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const void* img, const int* eA, void* xs,
+              int* maxb, const double* x, double* y, int* err, int wait_limit, cudaStream_t s);
 void mr_tuning(const MR& M, int level, int nlev, int32_t* out);
 
 // device_tc.cu: multi-right-hand-side smoother sweep y = x + omega (bh - x - Ahat x) on
 // tcgen05 tensor cores, Ahat BF16 [nnzb][np][np], vectors [n][np][R]; err set on a wait timeout
+// wait_limit: iteration limit of the waits inside the loop (< 0: the default)
 bool mr_tc_smooth(int np, int n, int R, const int* rowptr, const int* col, const void* Ahat_bf16, const float* x,
-                  const float* bh, float* y, float omega, int* err, cudaStream_t s);
+                  const float* bh, float* y, float omega, int* err, int wait_limit, cudaStream_t s);

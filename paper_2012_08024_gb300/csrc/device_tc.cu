@@ -16,8 +16,10 @@
 // between neighbouring core matrices along K, SBO = 512 bytes between groups
 // of 8 rows (4 core matrices cover the padded K = 16).  One thread issues the
 // MMAs and commits them to an mbarrier; every wait has an iteration limit,
-// after which the kernel sets the error flag, waits once more (bounded) for
-// its MMAs and frees its tensor memory.
+// after which the kernel sets the error flag, waits once more (bounded by the
+// default limit) for its MMAs and frees its tensor memory.  The limit of the
+// waits inside the loop is a kernel argument: a caller can lower it (0 makes
+// the first wait give up at once) to exercise that path without a fault.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -59,9 +61,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, int limit = kWaitLimit) {
   uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it)
+  for (int it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kTcRows) mr_tc_smooth_kernel(int n, int R, con
                                                                const __nv_bfloat16* __restrict__ Ahat,
                                                                const float* __restrict__ x,
                                                                const float* __restrict__ bh, float* __restrict__ y,
-                                                               float omega, int* __restrict__ err) {
+                                                               float omega, int* __restrict__ err, int wait_limit) {
   __shared__ __align__(1024) unsigned char sXhi[kTcRows * kTcK * 4];
   __shared__ __align__(1024) unsigned char sXlo[kTcRows * kTcK * 4];
   __shared__ __align__(1024) unsigned char sB[kTcK * kTcK * 4];
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(kTcRows) mr_tc_smooth_kernel(int n, int R, con
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
       }
-      ok = __syncthreads_and(wait_phase(mb, parity) ? 1 : 0) != 0;   // the same decision in every thread
+      ok = __syncthreads_and(wait_phase(mb, parity, wait_limit) ? 1 : 0) != 0;   // the same decision in every thread
       parity ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
     }
@@ -198,15 +200,16 @@ __global__ void __launch_bounds__(kTcRows) mr_tc_smooth_kernel(int n, int R, con
 }  // namespace
 
 bool mr_tc_smooth(int np, int n, int R, const int* rowptr, const int* col, const void* Ahat_bf16, const float* x,
-                  const float* bh, float* y, float omega, int* err, cudaStream_t s) {
+                  const float* bh, float* y, float omega, int* err, int wait_limit, cudaStream_t s) {
   const unsigned gy = (unsigned)((R + kTcRows - 1) / kTcRows);
   const unsigned gx = (unsigned)std::min(n, 152 * 8);
   const __nv_bfloat16* A = (const __nv_bfloat16*)Ahat_bf16;
+  const int lim = wait_limit < 0 ? kWaitLimit : std::min(wait_limit, kWaitLimit);
   switch (np) {
-    case 3: mr_tc_smooth_kernel<3><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err); break;
-    case 4: mr_tc_smooth_kernel<4><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err); break;
-    case 6: mr_tc_smooth_kernel<6><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err); break;
-    case 10: mr_tc_smooth_kernel<10><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err); break;
+    case 3: mr_tc_smooth_kernel<3><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err, lim); break;
+    case 4: mr_tc_smooth_kernel<4><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err, lim); break;
+    case 6: mr_tc_smooth_kernel<6><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err, lim); break;
+    case 10: mr_tc_smooth_kernel<10><<<dim3(gx, gy), kTcRows, 0, s>>>(n, R, rowptr, col, A, x, bh, y, omega, err, lim); break;
     default: return false;
   }
   count_launch();

@@ -1,7 +1,9 @@
 """Mixed precision (FP32 V-cycle inside the FP64 outer CG) against the FP64
 oracle.  The FP32 V-cycle is a different preconditioner from the FP64 one: its
-output differs by FP32 rounding (unit roundoff 6e-8, amplified by the smoother
-and transfers; bound used here 1e-4 relative).  The outer CG, its residual,
+output differs by FP32 rounding (unit roundoff u = 6e-8) of the restricted
+residuals, which the coarsest solve amplifies by up to cond(A_n) (7.5e5 on the
+triangle case: u cond(A_n) = 4.5e-2).  Measured: 1.1e-4 on the triangle case;
+bound used here 5e-4 relative.  The outer CG, its residual,
 dots and updates stay FP64, so the solution agrees with the FP64 oracle's to
 the solve tolerance: relative L2 difference <= 1e-9 and true residual
 <= 2e-10 ||b||.  The iteration count of the flexible (Polak-Ribiere) CG is
@@ -43,7 +45,7 @@ def test_fp32_vcycle_close_to_fp64_oracle(case):
     S.vcycle(_t(oc.to_tree(0, r)), z)
     err = rel(oc.to_work(0, z.cpu().numpy()), oc.V.apply(r))
     print(f"FP32 V-cycle relative error vs FP64 oracle: {err:.2e}")
-    assert err <= 1e-4
+    assert err <= 5e-4
 
 
 def test_mixed_solve_matches_fp64_oracle(case):

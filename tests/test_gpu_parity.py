@@ -65,6 +65,7 @@ def case(request):
     oc = OracleCase(mesh, kw["p"], kw["max_levels"], seed=kw.get("seed", 0))
     assert S.n_levels == oc.H.n_levels
     oc.setup = setup
+    oc.kw = kw
     return S, oc, mesh
 
 
@@ -145,6 +146,27 @@ def test_vcycle(case):
     z = torch.empty(len(r), dtype=torch.float64, device="cuda")
     S.vcycle(_t(oc.to_tree(0, r)), z)
     assert rel(oc.to_work(0, z.cpu().numpy()), oc.V.apply(r)) <= 1e-9 + 100 * oc.setup
+
+
+def test_fused_transfers_match_separate_kernels(case):
+    """The V-cycle with the fused residual + restriction (+ first coarse smoothing
+    step) and the prolongation carried by the coarse level's last sweep against
+    the same cycle with separate kernels: the same arithmetic except the order
+    of the per-agglomerate sums, whose rounding the coarsest solve amplifies by
+    at most cond(A_n); and both against the oracle."""
+    import torch
+    from paper_2012_08024_gb300 import Solver
+    S, oc, mesh = case
+    S2 = Solver(mesh, fuse_transfers=3, **oc.kw).bind()
+    Ae, _ = exported_operator(S, S.n_levels - 1)
+    cond = np.linalg.cond(Ae.toarray())
+    r = np.random.default_rng(31).standard_normal(oc.H.A[0].shape[0])
+    z1 = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    z2 = torch.empty_like(z1)
+    S.vcycle(_t(oc.to_tree(0, r)), z1)
+    S2.vcycle(_t(oc.to_tree(0, r)), z2)
+    d = rel(z1.cpu().numpy(), z2.cpu().numpy())
+    assert d <= 1e-13 + 10 * cond * EPS, (d, cond)
 
 
 def test_full_solve_matches_oracle(case):
