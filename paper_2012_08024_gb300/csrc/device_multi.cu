@@ -616,7 +616,7 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
     }
   };
   bool ok = true;
-  {
+  if (!M.oz) {   // the FP64 CUDA-core apply (the split apply has no variants)
     const DevLevel& L0 = D.lev[0];
     const size_t nv = (size_t)L0.n * np * R;
     cudaMemsetAsync(M.p, 0, nv * sizeof(double), s);

@@ -50,7 +50,7 @@ constexpr uint32_t kLBO = 128, kSBO = 256;    // bytes (BF16, K = 16)
 constexpr int kXBytes = kTile * 16 * 2;       // one X slice operand: 4 KB
 constexpr int kABytes = kBRows * 16 * 2;      // all A slices of one block: 4 KB
 constexpr int kStageBytes = kS * kXBytes + kABytes;
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kWaitLimit = 1 << 22;
 constexpr int kTmemCols = 16 * kS;            // accumulators d = 0 .. S-1, 16 columns each
 
@@ -121,47 +121,95 @@ __global__ void oz_colexp_kernel(size_t nrows, int R, const double* __restrict__
   atomicMax(maxb + r, m);
 }
 
-// xs[K][t][j][r] = slice t of x[K][j][r] (BF16 bits), the column scaled by 2^{-(maxb - 1022)}
-__global__ void oz_slice_kernel(size_t nrows, int np, int R, const double* __restrict__ x,
-                                const int* __restrict__ maxb, uint16_t* __restrict__ xs) {
-  const size_t tot = nrows * R;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t row = t / R;
-    const int r = (int)(t - row * R);
-    const size_t K = row / np;
-    const int j = (int)(row - K * np);
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x[t]);
-    const bool neg = (bits >> 63) != 0;
-    const int b = (int)((bits >> 52) & 0x7FF);
-    unsigned long long F = 0;   // |x| 2^{56 - E_X}, truncated: < 2^56
-    if (b != 0) {
-      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const int sh = b - maxb[r] + 3;   // <= 3
-      if (sh >= 0) F = M << sh;
-      else if (sh > -64) F = M >> (-sh);
-    }
-    uint16_t* o = xs + (K * kS * np + j) * (size_t)R + r;
+// Slices of x as MMA operand images: for element J, column tile c and slice t,
+// the 4 KB image of X_J^T (rows = the tile's 128 columns, K = 16 coefficients
+// j, zero beyond n_p and beyond R) at xs + ((J * tiles + c) * S + t) * 4 KB.
+// One thread per (J, column); the column is scaled by 2^{-(maxb - 1022)}.
+template <int NP>
+__global__ void oz_slice_kernel(int n, int R, int tiles, const double* __restrict__ x,
+                                const int* __restrict__ maxb, unsigned char* __restrict__ xs) {
+  const size_t tot = (size_t)n * tiles * kTile;
+  for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < tot; u += (size_t)gridDim.x * blockDim.x) {
+    const size_t J = u / ((size_t)tiles * kTile);
+    const int rr = (int)(u - J * tiles * kTile);
+    const int c = rr / kTile, row = rr - c * kTile;
+    const int r = rr;
+    uint32_t w[kS][8];
 #pragma unroll
-    for (int s = 0; s < kS; ++s)
-      o[(size_t)s * np * R] = (uint16_t)bf16_small((uint32_t)((F >> (49 - 7 * s)) & 127u), neg);
+    for (int t = 0; t < kS; ++t)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[t][q] = 0u;
+    if (r < R) {
+      const int mb = maxb[r];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(x[(J * NP + j) * (size_t)R + r]);
+        const bool neg = (bits >> 63) != 0;
+        const int b = (int)((bits >> 52) & 0x7FF);
+        unsigned long long F = 0;   // |x| 2^{56 - E_X}, truncated: < 2^56
+        if (b != 0) {
+          const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const int sh = b - mb + 3;   // <= 3
+          if (sh >= 0) F = M << sh;
+          else if (sh > -64) F = M >> (-sh);
+        }
+#pragma unroll
+        for (int t = 0; t < kS; ++t)
+          w[t][j >> 1] |= bf16_small((uint32_t)((F >> (49 - 7 * t)) & 127u), neg) << ((j & 1) * 16);
+      }
+    }
+    unsigned char* img = xs + ((J * tiles + c) * kS) * (size_t)kXBytes;
+#pragma unroll
+    for (int t = 0; t < kS; ++t) {
+      unsigned char* dst = img + t * kXBytes;
+      *reinterpret_cast<uint4*>(dst + kmaj16(row, 0)) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      *reinterpret_cast<uint4*>(dst + kmaj16(row, 8)) = make_uint4(w[t][4], w[t][5], w[t][6], w[t][7]);
+    }
   }
 }
 
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void arrive_expect(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// CTA (x, c) owns the block rows K = x, x + gridDim.x, ... and column tile c.
+// Thread 0 streams the blocks of those rows through a ring of kStages shared
+// memory stages: for each block it waits until the stage is free (the MMAs
+// that read it completed: empty[]), posts the expected bytes and two bulk
+// copies (the 32 KB X_J slice images and the block's 4 KB slice image) on
+// full[], and, kStages - 1 blocks later, waits on full[] and issues the
+// block's S MMAs, committed to empty[].  At the end of a row it commits to
+// rowbar; all threads wait there and run the epilogue.
 template <int NP>
-__global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, int tiles, const int* __restrict__ rowptr,
                                                          const int* __restrict__ col,
-                                                         const uint16_t* __restrict__ Asl,
-                                                         const int* __restrict__ eA, const uint16_t* __restrict__ xs,
+                                                         const unsigned char* __restrict__ Aimg,
+                                                         const int* __restrict__ eA,
+                                                         const unsigned char* __restrict__ xs,
                                                          const int* __restrict__ maxb, double* __restrict__ y,
                                                          int* __restrict__ err, int wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], rowbar;
   __shared__ uint32_t tmem_base;
+  __shared__ int fail_s;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int r = blockIdx.y * kTile + tid;   // this thread's column
+  const int c = blockIdx.y;
+  const int r = c * kTile + tid;   // this thread's column
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[s])));
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&rowbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    fail_s = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -173,63 +221,81 @@ __global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, const int
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int ex = r < R ? maxb[r] - 1022 : 0;   // E_X of this column
-  uint32_t phase[kStages] = {0u, 0u};
-  bool busy[kStages] = {false, false};
-  int g = 0;
+  // producer cursor (thread 0): the next block to copy, as (row, block)
+  int pk = blockIdx.x, pb = pk < n ? rowptr[pk] : 0;
+  long long issued = 0, consumed = 0;   // blocks copied / blocks whose MMAs are issued
+  int rows_done = 0;                    // rowbar waits made by every thread
+  int rb_commits = 0, rb_seen = 0;      // thread 0: rowbar commits, and phases it saw complete
   bool ok = true;
-  for (int K = blockIdx.x; K < n && ok; K += gridDim.x) {
+  auto advance = [&]() {   // the producer cursor to the next block of this CTA's rows
+    while (pk < n && pb >= rowptr[pk + 1]) {
+      pk += gridDim.x;
+      pb = pk < n ? rowptr[pk] : 0;
+    }
+  };
+  auto issue = [&]() -> bool {   // copies of the block at the cursor into stage issued % kStages
+    advance();
+    if (pk >= n) return true;
+    const int st = (int)(issued % kStages);
+    if (issued >= kStages &&
+        !wait_phase(smem_u32(&empty[st]), (uint32_t)(((issued / kStages) - 1) & 1), wait_limit))
+      return false;
+    unsigned char* sx = smem + st * kStageBytes;
+    const uint32_t fb = smem_u32(&full[st]);
+    arrive_expect(fb, (uint32_t)kStageBytes);
+    bulk_g2s(sx, xs + ((size_t)col[pb] * tiles + c) * kS * (size_t)kXBytes, (uint32_t)(kS * kXBytes), fb);
+    bulk_g2s(sx + kS * kXBytes, Aimg + (size_t)pb * kABytes, (uint32_t)kABytes, fb);
+    ++issued;
+    ++pb;
+    return true;
+  };
+  for (int K = blockIdx.x; K < n; K += gridDim.x) {
     const int b0 = rowptr[K], b1 = rowptr[K + 1];
-    for (int bb = b0; bb < b1 && ok; ++bb, ++g) {
-      const int st = g & 1;
-      if (busy[st]) {   // the MMAs that last read this stage
-        ok = __syncthreads_and(wait_phase(smem_u32(&bar[st]), phase[st], wait_limit) ? 1 : 0) != 0;
-        phase[st] ^= 1u;
-        busy[st] = false;
-        if (!ok) break;
-      }
-      unsigned char* sx = smem + st * kStageBytes;
-      unsigned char* sa = sx + kS * kXBytes;
-      const int J = col[bb];
-      // X_J^T slices: row = this column, K = j (zero beyond n_p and beyond R)
-#pragma unroll
-      for (int t = 0; t < kS; ++t) {
-        uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        if (r < R) {
-          const uint16_t* src = xs + ((size_t)J * kS * NP + (size_t)t * NP) * R + r;
-#pragma unroll
-          for (int j = 0; j < NP; ++j) w[j >> 1] |= (uint32_t)src[(size_t)j * R] << ((j & 1) * 16);
+    if (tid == 0 && ok) {
+      for (int bb = b0; bb < b1 && ok; ++bb) {
+        while (ok && issued < consumed + kStages) {
+          const long long before = issued;
+          ok = issue();
+          if (issued == before) break;   // no block left to copy
         }
-        unsigned char* dst = sx + t * kXBytes;
-        *reinterpret_cast<uint4*>(dst + kmaj16(tid, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(dst + kmaj16(tid, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
-      }
-      // the block's B operand image (4 KB)
-      const uint4* ai = reinterpret_cast<const uint4*>(Asl + (size_t)bb * (kABytes / 2));
-      reinterpret_cast<uint4*>(sa)[tid] = __ldg(ai + tid);
-      reinterpret_cast<uint4*>(sa)[tid + kTile] = __ldg(ai + tid + kTile);
-      asm volatile("fence.proxy.async.shared::cta;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
-        const uint64_t bdesc = smem_desc(smem_u32(sa));
+        if (!ok) break;
+        const int st = (int)(consumed % kStages);
+        if (!wait_phase(smem_u32(&full[st]), (uint32_t)((consumed / kStages) & 1), wait_limit)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        unsigned char* sx = smem + st * kStageBytes;
+        const uint64_t bdesc = smem_desc(smem_u32(sx + kS * kXBytes));
 #pragma unroll
         for (int t = 0; t < kS; ++t)
           mma_bf16(tmem + (uint32_t)(16 * t), smem_desc(smem_u32(sx + t * kXBytes)), bdesc, idesc_bf16(16 * (kS - t)),
                    (bb > b0 || t > 0) ? 1u : 0u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&bar[st])));
+            smem_u32(&empty[st])));
+        ++consumed;
       }
-      busy[st] = true;
+      if (ok && b1 > b0) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&rowbar)));
+        ++rb_commits;
+      }
+      if (!ok) fail_s = 1;
     }
-    // the row's MMAs complete
-    for (int st = 0; st < kStages && ok; ++st) {
-      if (!busy[st]) continue;
-      ok = __syncthreads_and(wait_phase(smem_u32(&bar[st]), phase[st], wait_limit) ? 1 : 0) != 0;
-      phase[st] ^= 1u;
-      busy[st] = false;
+    __syncthreads();
+    if (fail_s) {
+      ok = false;
+      break;
     }
-    if (!ok) break;
+    if (b1 > b0) {
+      if (!wait_phase(smem_u32(&rowbar), (uint32_t)(rows_done & 1), wait_limit)) ok = false;
+      else if (tid == 0) ++rb_seen;
+      ++rows_done;
+    }
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      ok = false;
+      break;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: y[K][i][r] = 2^{E_A + E_X - 63} sum_d acc_d 2^{7 (S - 1 - d)}, in two halves of i
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -265,9 +331,18 @@ __global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, const int
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    for (int st = 0; st < kStages; ++st)   // MMAs still running on a stage
-      if (busy[st]) wait_phase(smem_u32(&bar[st]), phase[st], kWaitLimit);
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // copies in flight land in shared memory and issued MMAs finish before the
+      // CTA ends: wait for both (default limit), every phase in order (a parity
+      // wait two phases behind would not wait)
+      for (long long u = consumed; u < issued; ++u)
+        wait_phase(smem_u32(&full[u % kStages]), (uint32_t)((u / kStages) & 1), kWaitLimit);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&rowbar)));
+      ++rb_commits;
+      for (int ph = rb_seen; ph < rb_commits; ++ph) wait_phase(smem_u32(&rowbar), (uint32_t)(ph & 1), kWaitLimit);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -292,8 +367,10 @@ uint16_t host_bf16_int(int k) {
 }  // namespace
 
 size_t oz_image_bytes(const cdg::BSR& A) { return (size_t)A.nnzb() * kABytes; }
-size_t oz_xslice_bytes(int64_t n, int np, int R) { return (size_t)n * kS * np * R * sizeof(uint16_t); }
-int oz_smem_bytes() { return kStages * kStageBytes; }
+size_t oz_xslice_bytes(int64_t n, int np, int R) {
+  (void)np;
+  return (size_t)n * ((R + kTile - 1) / kTile) * kS * kXBytes;
+}
 
 // The split is exact when every FP32 accumulator stays an integer below 2^23
 // (below 2^24 for exact FP32 sums, one bit more of headroom for the int32
@@ -341,22 +418,22 @@ bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const voi
   cudaMemsetAsync(maxb, 0, sizeof(int) * R, s);
   const unsigned ty = (unsigned)((R + 255) / 256);
   oz_colexp_kernel<<<dim3(2 * 152, ty), 256, 0, s>>>(nrows, R, x, maxb);
-  oz_slice_kernel<<<4 * 152 * 4, 256, 0, s>>>(nrows, np, R, x, maxb, (uint16_t*)xs);
+  const int tiles = (R + kTile - 1) / kTile;
   const int lim = wait_limit < 0 ? kWaitLimit : std::min(wait_limit, kWaitLimit);
-  // three CTAs per SM (72 KB of shared memory, 128 TMEM columns each): the whole grid is resident
-  const unsigned tiles = (unsigned)((R + kTile - 1) / kTile);
-  const dim3 grid((unsigned)std::max(1, std::min(n, (int)(152 * 3 / tiles))), tiles);
-  const int smem = oz_smem_bytes();
-  auto go = [&](auto kern) {
+  // two CTAs per SM (108 KB of shared memory, 128 TMEM columns each): the whole grid is resident
+  const dim3 grid((unsigned)std::max(1, std::min(n, 152 * 2 / tiles)), (unsigned)tiles);
+  const int smem = kStages * kStageBytes;
+  auto go = [&](auto slice, auto kern) {
+    slice<<<4 * 152 * 4, 256, 0, s>>>(n, R, tiles, x, maxb, (unsigned char*)xs);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, kTile, smem, s>>>(n, R, rowptr, col, (const uint16_t*)img, eA, (const uint16_t*)xs, maxb, y, err,
-                                   lim);
+    kern<<<grid, kTile, smem, s>>>(n, R, tiles, rowptr, col, (const unsigned char*)img, eA,
+                                   (const unsigned char*)xs, maxb, y, err, lim);
   };
   switch (np) {
-    case 3: go(oz_apply_kernel<3>); break;
-    case 4: go(oz_apply_kernel<4>); break;
-    case 6: go(oz_apply_kernel<6>); break;
-    case 10: go(oz_apply_kernel<10>); break;
+    case 3: go(oz_slice_kernel<3>, oz_apply_kernel<3>); break;
+    case 4: go(oz_slice_kernel<4>, oz_apply_kernel<4>); break;
+    case 6: go(oz_slice_kernel<6>, oz_apply_kernel<6>); break;
+    case 10: go(oz_slice_kernel<10>, oz_apply_kernel<10>); break;
     default: return false;
   }
   count_launch(3);
