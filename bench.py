@@ -241,6 +241,8 @@ def run_extras(pkg, dev, stream, barrier, only=None):
         out.update(extra_batched(pkg, dev, stream))
     if only in (None, "multi_rhs"):
         out.update(extra_multi_rhs(pkg, dev, stream))
+    if only == "tc_small":
+        out.update(extra_tc_small(pkg, dev, stream))
     if only in ("multi_rhs_bf16", "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply"):
         out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))   # one variant
     if only in (None, "adjoint"):
@@ -293,6 +295,28 @@ def extra_latency_tri32(pkg, dev, stream):
     ms, (u, h, it, rc) = _time(lambda: S.solve(fq), stream, 20)
     return {"tri32_p2_latency": {"ms_per_solve": ms, "iterations": it, "rc": rc, "dofs": S.info["n_dofs"],
                                  "us_per_iteration": ms * 1e3 / max(it, 1)}}
+
+
+def extra_tc_small(pkg, dev, stream):
+    """A small case of the tensor-core kernels (the size ncu captures in full):
+    100 x 100 square (20,000 triangles, p = 3, 200,000 dofs), 128 right-hand
+    sides (x: 205 MB FP64, above L2): three split FP64 applies (tc_fp64_apply),
+    then one BF16-block multi-RHS solve of two iterations (tcgen05 sweeps)."""
+    import torch
+    from synthetic import jittered_square, sine_combination_sources
+    mesh = jittered_square(100)
+    R = 128
+    S = pkg.Solver(mesh, p=3, max_levels=4, precision="fp32", nrhs=R, tc_fp64_apply=True).bind(dev)
+    x = torch.tensor(np.random.default_rng(1).standard_normal((S.info["n_dofs"], R)), device=dev)
+    y = torch.empty_like(x)
+    ms, _ = _time(lambda: S.apply_multi(x, y), stream, 2)
+    del S, x, y
+    S = pkg.Solver(mesh, p=3, max_levels=4, nu_pre=2, nu_post=2, precision="bf16", nrhs=R, maxit=2,
+                   tensor_cores=True).bind(dev)
+    fq = torch.tensor(sine_combination_sources(S.quadrature_points()[0], R, mmax=8, seed0=0), device=dev)
+    S.solve_multi(fq)
+    torch.cuda.synchronize(dev)
+    return {"tc_small": {"split_fp64_apply_ms": ms, "dofs": int(mesh.n_elements * 10), "nrhs": R}}
 
 
 def extra_batched(pkg, dev, stream):
@@ -463,7 +487,7 @@ def main():
                          "kernels; the form a kernel profiler lists launch by launch)")
     ap.add_argument("--only-extra", default=None,
                     choices=["latency", "batched", "multi_rhs", "adjoint", "tet48", "multi_rhs_bf16",
-                             "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply"],
+                             "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply", "tc_small"],
                     help="run one extra workload alone and print its numbers (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -144,7 +144,7 @@ size_t layout(const cdg::Hierarchy& H, int precision, int nrhs, DeviceState* S, 
   }
   D.nc = (int)(H.lev.back().n * D.lev[nlev - 1].np);
   D.nseg = (int)H.seg_rows[0].size() - 1;
-  D.bps = std::max(1, kDotBlocks / D.nseg);
+  D.bps = D.nseg == 1 ? kDotBlocks1 : std::max(1, kDotBlocks / D.nseg);
   D.seg_dof = c.take<long long>(D.nseg + 1);
   D.crow_seg = c.take<int>(D.nc);
   D.crow_off = c.take<int>(D.nseg + 1);
@@ -517,8 +517,26 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(const long long* __restri
   int seg;
   size_t lo, hi;
   seg_range(seg_dof, bps, seg, lo, hi);
+  // four elements' loads in flight per step; the sums run over the thread's
+  // elements in ascending order (the rounding does not depend on the unrolling)
   double s = 0.0, s2 = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  const size_t bd = blockDim.x;
+  size_t i = lo + threadIdx.x;
+  for (; i + 3 * bd < hi; i += 4 * bd) {
+    double xv[4], yv[4], wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xv[u] = x[i + u * bd];
+      yv[u] = y[i + u * bd];
+      wv[u] = w ? w[i + u * bd] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s = fma(xv[u], yv[u], s);
+      if (w) s2 = fma(xv[u], wv[u], s2);
+    }
+  }
+  for (; i < hi; i += bd) {
     s = fma(x[i], y[i], s);
     if (w) s2 = fma(x[i], w[i], s2);
   }
@@ -600,7 +618,26 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(const long long* __
   seg_range(seg_dof, bps, seg, lo, hi);
   const double alpha = scal[(size_t)seg * S_COUNT + S_ALPHA];
   double s = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  const size_t bd = blockDim.x;
+  size_t i = lo + threadIdx.x;
+  for (; i + 3 * bd < hi; i += 4 * bd) {   // four elements' loads in flight, ascending sum
+    double pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[i + u * bd];
+      qv[u] = q[i + u * bd];
+      xv[u] = x[i + u * bd];
+      rv[u] = r[i + u * bd];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[i + u * bd] = fma(alpha, pv[u], xv[u]);
+      const double ri = fma(-alpha, qv[u], rv[u]);
+      r[i + u * bd] = ri;
+      s = fma(ri, ri, s);
+    }
+  }
+  for (; i < hi; i += bd) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -649,7 +686,19 @@ __global__ void __launch_bounds__(kThreads) cg_p_kernel(const long long* __restr
   size_t lo, hi;
   seg_range(seg_dof, bps, seg, lo, hi);
   const double beta = first ? 0.0 : scal[(size_t)seg * S_COUNT + S_BETA];
-  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+  const size_t bd = blockDim.x;
+  size_t i = lo + threadIdx.x;
+  for (; i + 3 * bd < hi; i += 4 * bd) {
+    double zv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zv[u] = z[i + u * bd];
+      pv[u] = first ? 0.0 : p[i + u * bd];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * bd] = first ? zv[u] : fma(beta, pv[u], zv[u]);
+  }
+  for (; i < hi; i += bd) p[i] = first ? z[i] : fma(beta, p[i], z[i]);
 }
 
 // b (tree order, or user order) from f at volume points and g_D / g_N at boundary points
@@ -873,9 +922,14 @@ bool launch_smooth_first(int np, int n, const T* Dinv, const T* b, T* bh, T* x, 
   return true;
 }
 
+// 64-thread CTAs: a warp's loop runs to the largest child count among its
+// agglomerates, and small CTAs spread that uneven work over the SMs more evenly
 template <typename T>
 bool launch_restrict(int np, int nc, const int* cp, const T* L, const T* r, T* bc, cudaStream_t s) {
-  CDG_NP_DISPATCH(np, launch(restrict_kernel<T, NP>, rows_grid(nc, np), kThreads, s, nc, cp, L, r, bc));
+  constexpr int kRT = 64;
+  const int64_t warps = ((int64_t)nc + 32 / np - 1) / (32 / np);
+  const unsigned g = (unsigned)std::max<int64_t>(1, (warps * 32 + kRT - 1) / kRT);
+  CDG_NP_DISPATCH(np, launch(restrict_kernel<T, NP>, g, kRT, s, nc, cp, L, r, bc));
   return true;
 }
 

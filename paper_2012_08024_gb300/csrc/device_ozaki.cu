@@ -22,11 +22,12 @@
 // of the MMA B operand (128 rows s * 16 + i, K = 16 columns j, canonical
 // K-major SWIZZLE_NONE core matrices: 8 rows x 16 bytes, LBO = 128 bytes
 // along K, SBO = 256 bytes between 8-row groups); X is sliced once per apply
-// into [n][S][n_p][R] BF16 and staged per block as S operands A = X_J^T
-// (128 columns x 16, same layout).  One CTA of 128 threads owns a tile of 128
-// columns; one thread issues the MMAs of a block and commits them to the
-// mbarrier of its shared-memory stage (two stages, so staging the next block
-// overlaps the MMAs of the current one).  Every wait has an iteration limit;
+// into the same images, 4 KB per (element, column tile, slice), and staged per
+// block as S operands A = X_J^T (128 columns x 16).  One CTA of 128 threads
+// owns a tile of 128 columns; one thread copies the operands of a block into a
+// ring of three shared-memory stages with bulk copies, issues its MMAs and
+// commits them to the stage's mbarrier, so the copies of the next blocks
+// overlap the MMAs of the current one.  Every wait has an iteration limit;
 // on expiry the kernel sets the error flag, drains its MMAs (default limit),
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>

@@ -10,7 +10,8 @@
 
 constexpr int kMaxLev = CDG_MAX_LEVELS;
 constexpr int kThreads = 256;
-constexpr int kDotBlocks = 2 * 152;   // fixed grid for deterministic reductions
+constexpr int kDotBlocks = 8 * 152;   // fixed grid of the vector kernels of batched handles (8 CTAs per SM)
+constexpr int kDotBlocks1 = 2 * 152;  // the same for single-mesh handles (their dot partials: 2 CTAs per SM)
 
 // per-segment CG scalars (one row of S_COUNT doubles per mesh of the handle)
 // S_HDONE: the segment's residual history is closed (single-graph solve)

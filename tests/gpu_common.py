@@ -29,3 +29,4 @@ class OracleCase:
 def rel(a, b):
     a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+

@@ -78,13 +78,14 @@ def test_gmres_matches_oracle(case):
     assert abs(it - ito) <= 1, (it, ito, hist[-3:], ho[-3:])
     k = min(it, ito)
     ho = np.asarray(ho)
-    assert np.all(np.abs(hist[:k] - ho[:k]) <= 1e-6 * ho[:k] + 1e-13), (hist[:k], ho[:k])
     ug = u.cpu().numpy().ravel()
-    # the last entry is the true residual of the returned solution, up to the
-    # rounding of b - A u (1e-14 of |A| |u|: the two operators agree to 1e-14)
+    # residuals recomputed at a restart or at the end carry the rounding of
+    # b - A u (1e-14 of |A| |u|: the two operators agree to 1e-14)
     bn = np.linalg.norm(b)
     true_res = np.linalg.norm(b - H.A[0] @ ug) / bn
     rounding = 1e-14 * np.linalg.norm(abs(H.A[0]) @ np.abs(ug)) / bn
+    assert np.all(np.abs(hist[:k] - ho[:k]) <= 1e-6 * ho[:k] + max(1e-13, rounding)), (hist[:k], ho[:k], rounding)
+    # the last entry is the true residual of the returned solution, up to that rounding
     assert abs(hist[-1] - true_res) <= 1e-6 * true_res + rounding, (hist[-1], true_res, rounding)
     assert true_res <= 2 * tol
     if it == ito:
