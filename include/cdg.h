@@ -194,13 +194,15 @@ int cdg_batch_offsets(const cdg_handle* h, int32_t* n_meshes, int64_t* elem_offs
 const char* cdg_last_error(const cdg_handle* h);
 int cdg_query(const cdg_handle* h, cdg_info* info);
 /* Launch configuration chosen by the autotuner for one level (no counterpart in
- * the paper; an execution detail of this library).  out[10]: [0] FP64 level-0
+ * the paper; an execution detail of this library).  out[13]: [0] FP64 level-0
  * apply and [1] FP64 level-0 residual (level 0 only), [2] V-cycle residual and
  * [3] V-cycle smoother sweep (V-cycle precision): blocks in flight per step of
- * the vector-load kernel; multi-right-hand-side kernels as (right-hand-side
- * tile width, block rows per CTA): [4,5] smoother sweep, [6,7] residual,
- * [8,9] FP64 level-0 apply (level 0 only).  0 = not applicable or not tuned
- * yet.  Errors: CDG_EINVAL (bad level or NULL), CDG_ESTATE (not bound). */
+ * the vector-load kernel; multi-right-hand-side kernels as (threads across
+ * the right-hand sides, block rows per CTA): [4,5] smoother sweep, [6,7]
+ * residual, [8,9] FP64 level-0 apply (level 0 only), and their right-hand
+ * sides per thread: [10] smoother sweep, [11] residual, [12] FP64 level-0
+ * apply.  0 = not applicable or not tuned yet.  Errors: CDG_EINVAL (bad level
+ * or NULL), CDG_ESTATE (not bound). */
 int cdg_tuning(const cdg_handle* h, int32_t level, int32_t* out);
 
 /* Quadrature points at which the caller samples f, g_D and g_N (R3: collapsed

@@ -296,10 +296,11 @@ class Solver:
         """Autotuned launch configuration per level (cdg_tuning)."""
         keys = ("apply64_unroll", "residual64_unroll", "vcycle_residual_unroll", "vcycle_smoother_unroll",
                 "multi_smoother_tile", "multi_smoother_rows", "multi_residual_tile", "multi_residual_rows",
-                "multi_apply64_tile", "multi_apply64_rows")
+                "multi_apply64_tile", "multi_apply64_rows", "multi_smoother_cols", "multi_residual_cols",
+                "multi_apply64_cols")
         out = []
         for l in range(self.n_levels):
-            a = (C.c_int32 * 10)()
+            a = (C.c_int32 * 13)()
             self._check(lib().cdg_tuning(self._h, l, a))
             out.append({k: int(v) for k, v in zip(keys, a) if v})
         return out

@@ -1490,7 +1490,7 @@ static int autotune_bsr(cdg_handle* h, cudaStream_t s) {
 }
 
 int dev_tuning(const cdg_handle* h, int level, int32_t* out) {
-  for (int k = 0; k < 10; ++k) out[k] = 0;
+  for (int k = 0; k < 13; ++k) out[k] = 0;
   const DeviceState& D = *h->dev;
   const DevLevel& L = D.lev[level];
   const bool vec = L.np % 2 == 0;

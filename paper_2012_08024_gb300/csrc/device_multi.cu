@@ -42,21 +42,25 @@ __device__ __forceinline__ void stage_block(TC* s, const TA* a, int ne) {
 }
 
 // y = A x (MODE 0), y = b - A x (1), y = x + omega (b - x - A x) (3; A = Ahat, b = D^-1 b).
-// A CTA of blockDim (TX, BR) owns BR consecutive block rows and one tile of TX
-// right-hand sides: row group threadIdx.y stages its blocks in shared memory
-// and thread x applies them to column blockIdx.y * TX + x.  TX and BR are the
-// autotuned right-hand-side tile width and block-row tiling; every choice sums
+// A CTA of blockDim (TX, BR) owns BR consecutive block rows and one tile of
+// TX C right-hand sides: row group threadIdx.y stages its blocks in shared
+// memory and thread x applies them to columns x + c TX (c < C) of the tile.
+// Each block value read from shared memory feeds C fused multiply-adds, so
+// with C = 1 the shared-memory reads, not the FMA pipe, set the pace.  TX, BR
+// and C are the autotuned right-hand-side tile; every choice sums each column
 // in the same order, so they change the timing only.
-template <typename TA, typename TV, typename TC, int NP, int MODE, int BR>
+constexpr int kMrMaxBR = 4;
+
+template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
 __global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
                               const TA* __restrict__ A, const TV* __restrict__ x, const TV* __restrict__ b,
                               TV* __restrict__ y, TC omega) {
-  __shared__ TC as[BR][NP * NP];
+  __shared__ __align__(16) TC as[kMrMaxBR][NP * NP];
+  const int BR = (int)blockDim.y, TX = (int)blockDim.x;
   const int K0 = blockIdx.x * BR;
   const int K = K0 + threadIdx.y;
-  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * TX * C + threadIdx.x;
   int b0 = 0, nb = 0, nbmax = 0;
-#pragma unroll
   for (int q = 0; q < BR; ++q) {
     if (K0 + q < n) {
       const int a0 = rowptr[K0 + q], cnt = rowptr[K0 + q + 1] - a0;
@@ -67,32 +71,47 @@ __global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, cons
       }
     }
   }
-  TC acc[NP];
+  TC acc[C][NP];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) acc[i] = TC(0);
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc[c][i] = TC(0);
   for (int t = 0; t < nbmax; ++t) {
     __syncthreads();
     if (t < nb) stage_block<TA, TC>(as[threadIdx.y], A + (size_t)(b0 + t) * NP * NP, NP * NP);
     __syncthreads();
-    if (t < nb && r < R) {
-      const TV* xj = x + (size_t)col[b0 + t] * NP * R + r;
-      TC xv[NP];
+    if (t < nb) {
+      const TV* xj = x + (size_t)col[b0 + t] * NP * R;
+      TC xv[C][NP];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) xv[j] = (TC)xj[(size_t)j * R];
+      for (int c = 0; c < C; ++c) {
+        const int r = r0 + c * TX;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) xv[c][j] = r < R ? (TC)xj[(size_t)j * R + r] : TC(0);
+      }
 #pragma unroll
       for (int i = 0; i < NP; ++i)
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[i] = fma(as[threadIdx.y][i * NP + j], xv[j], acc[i]);
+        for (int j = 0; j < NP; ++j) {
+          const TC a = as[threadIdx.y][i * NP + j];
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[c][i] = fma(a, xv[c][j], acc[c][i]);
+        }
     }
   }
-  if (K >= n || r >= R) return;
-  const size_t base = (size_t)K * NP * R + r;
+  if (K >= n) return;
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    const size_t o = base + (size_t)i * R;
-    if (MODE == 0) y[o] = (TV)acc[i];
-    else if (MODE == 1) y[o] = (TV)((TC)b[o] - acc[i]);
-    else y[o] = (TV)((TC)x[o] + omega * ((TC)b[o] - (TC)x[o] - acc[i]));
+  for (int c = 0; c < C; ++c) {
+    const int r = r0 + c * TX;
+    if (r >= R) continue;
+    const size_t base = (size_t)K * NP * R + r;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const size_t o = base + (size_t)i * R;
+      if (MODE == 0) y[o] = (TV)acc[c][i];
+      else if (MODE == 1) y[o] = (TV)((TC)b[o] - acc[c][i]);
+      else y[o] = (TV)((TC)x[o] + omega * ((TC)b[o] - (TC)x[o] - acc[c][i]));
+    }
   }
 }
 
@@ -192,17 +211,46 @@ __global__ void mr_convert_kernel(size_t n, const TI* __restrict__ a, TO* __rest
     b[i] = (TO)a[i];
 }
 
-// per-column partial dots over a chunk of rows: partial[g][r] (and [G + g][r] for w)
-__global__ void mr_dot_kernel(int nrows, int R, int G, const double* __restrict__ x, const double* __restrict__ y,
-                              const double* __restrict__ w, double* __restrict__ partial) {
+// The per-column vector kernels of the outer CG share one partition: CTA g of
+// G owns rows [nrows g / G, nrows (g + 1) / G) and thread r one column, so a
+// column's partial sums run over its rows in ascending order whichever kernel
+// forms them.  Rows go four at a time, all loads of a group before its
+// arithmetic, to keep enough loads in flight per thread.
+__device__ __forceinline__ void mr_rows(int nrows, int G, int g, int& lo, int& hi) {
+  lo = (int)((long long)nrows * g / G);
+  hi = (int)((long long)nrows * (g + 1) / G);
+}
+
+// per-column partial dots over a chunk of rows: partial[g][r] = sum x y (and
+// partial[G + g][r] = sum x w); Y is FP64 or FP32 (a V-cycle output, widened exactly)
+template <typename TY>
+__global__ void mr_dot_kernel(int nrows, int R, int G, const double* __restrict__ x, const TY* __restrict__ y,
+                              const TY* __restrict__ w, double* __restrict__ partial) {
   const int g = blockIdx.x, r = threadIdx.x;
   if (r >= R) return;
-  const int lo = (int)((long long)nrows * g / G), hi = (int)((long long)nrows * (g + 1) / G);
+  int lo, hi;
+  mr_rows(nrows, G, g, lo, hi);
   double s = 0.0, s2 = 0.0;
-  for (int row = lo; row < hi; ++row) {
+  int row = lo;
+  for (; row + 4 <= hi; row += 4) {
+    double xv[4], yv[4], wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t o = (size_t)(row + u) * R + r;
+      xv[u] = x[o];
+      yv[u] = (double)y[o];
+      wv[u] = w ? (double)w[o] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s = fma(xv[u], yv[u], s);
+      if (w) s2 = fma(xv[u], wv[u], s2);
+    }
+  }
+  for (; row < hi; ++row) {
     const size_t o = (size_t)row * R + r;
-    s = fma(x[o], y[o], s);
-    if (w) s2 = fma(x[o], w[o], s2);
+    s = fma(x[o], (double)y[o], s);
+    if (w) s2 = fma(x[o], (double)w[o], s2);
   }
   partial[(size_t)g * R + r] = s;
   if (w) partial[(size_t)(G + g) * R + r] = s2;
@@ -248,22 +296,72 @@ __global__ void mr_finalize_kernel(int R, int G, const double* __restrict__ part
   }
 }
 
-// x += alpha_r p; r -= alpha_r q (per column) -- and p = z + beta_r p
-__global__ void mr_update_kernel(size_t nrows, int R, const double* __restrict__ scal, const double* __restrict__ p,
-                                 const double* __restrict__ q, double* __restrict__ x, double* __restrict__ res) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nrows * R; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t % R);
-    const double a = scal[(size_t)r * S_COUNT + S_ALPHA];
-    x[t] = fma(a, p[t], x[t]);
-    res[t] = fma(-a, q[t], res[t]);
+// x += alpha_r p; r -= alpha_r q per column, with the FP32 copy of r that the
+// V-cycle reads and the partial r.r of the chunk (the sum mr_dot_kernel forms)
+__global__ void mr_update_kernel(int nrows, int R, int G, const double* __restrict__ scal,
+                                 const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                                 double* __restrict__ res, float* __restrict__ r32, double* __restrict__ partial) {
+  const int g = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  int lo, hi;
+  mr_rows(nrows, G, g, lo, hi);
+  const double a = scal[(size_t)r * S_COUNT + S_ALPHA];
+  double s = 0.0;
+  int row = lo;
+  for (; row + 4 <= hi; row += 4) {
+    double pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t o = (size_t)(row + u) * R + r;
+      pv[u] = p[o];
+      qv[u] = q[o];
+      xv[u] = x[o];
+      rv[u] = res[o];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t o = (size_t)(row + u) * R + r;
+      x[o] = fma(a, pv[u], xv[u]);
+      const double v = fma(-a, qv[u], rv[u]);
+      res[o] = v;
+      r32[o] = (float)v;
+      s = fma(v, v, s);
+    }
   }
+  for (; row < hi; ++row) {
+    const size_t o = (size_t)row * R + r;
+    x[o] = fma(a, p[o], x[o]);
+    const double v = fma(-a, q[o], res[o]);
+    res[o] = v;
+    r32[o] = (float)v;
+    s = fma(v, v, s);
+  }
+  partial[(size_t)g * R + r] = s;
 }
 
-__global__ void mr_p_kernel(size_t nrows, int R, const double* __restrict__ scal, int first,
-                            const double* __restrict__ z, double* __restrict__ p) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nrows * R; t += (size_t)gridDim.x * blockDim.x) {
-    const double beta = first ? 0.0 : scal[(size_t)(t % R) * S_COUNT + S_BETA];
-    p[t] = first ? z[t] : fma(beta, p[t], z[t]);
+// p = z + beta_r p per column (p = z on the first step); z is the V-cycle's FP32 output
+__global__ void mr_p_kernel(int nrows, int R, int G, const double* __restrict__ scal, int first,
+                            const float* __restrict__ z, double* __restrict__ p) {
+  const int g = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  int lo, hi;
+  mr_rows(nrows, G, g, lo, hi);
+  const double beta = first ? 0.0 : scal[(size_t)r * S_COUNT + S_BETA];
+  int row = lo;
+  for (; row + 4 <= hi; row += 4) {
+    double zv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t o = (size_t)(row + u) * R + r;
+      zv[u] = (double)z[o];
+      pv[u] = first ? 0.0 : p[o];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[(size_t)(row + u) * R + r] = first ? zv[u] : fma(beta, pv[u], zv[u]);
+  }
+  for (; row < hi; ++row) {
+    const size_t o = (size_t)row * R + r;
+    p[o] = first ? (double)z[o] : fma(beta, p[o], (double)z[o]);
   }
 }
 
@@ -311,14 +409,17 @@ struct MR {
   int R = 0, G = 0;
   bool bf16 = false;
   MRLevel lev[kMaxLev];
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr, *zold = nullptr;
-  float *r32 = nullptr, *z32 = nullptr;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *bt = nullptr;
+  // FP32 V-cycle input r32 and output z32; z32old holds the previous output
+  // (flexible CG), the two swap roles every step
+  float *r32 = nullptr, *z32 = nullptr, *z32old = nullptr;
   double* scal = nullptr;      // [R][S_COUNT]
   double* partial = nullptr;   // [2G][R]
   // autotuned (right-hand-side tile width, block rows per CTA) of mr_bsr_kernel per
   // level and mode (0 FP64 level-0 apply, 1 residual, 3 smoother sweep); 0 = not tuned
   int tile[kMaxLev][4] = {};
   int rows[kMaxLev][4] = {};
+  int cols[kMaxLev][4] = {};   // right-hand sides per thread
   bool tuned = false;
   bool tc = false;             // smoother sweeps on tcgen05 (BF16 blocks)
   int* tc_err = nullptr;       // set by a tensor-core kernel whose wait timed out
@@ -338,10 +439,13 @@ void mr_tuning(const MR& M, int level, int nlev, int32_t* out) {
     out[5] = M.rows[level][3];
     out[6] = M.tile[level][1];
     out[7] = M.rows[level][1];
+    out[10] = M.cols[level][3];
+    out[11] = M.cols[level][1];
   }
   if (level == 0) {
     out[8] = M.tile[0][0];
     out[9] = M.rows[0][0];
+    out[12] = M.cols[0][0];
   }
 }
 
@@ -407,13 +511,12 @@ size_t mr_layout(const cdg::Hierarchy& H, int R, int precision, int tc_fp64, MR*
   const size_t nv = (size_t)H.mesh.ne * np * R;
   M.x = c.take<double>(nv);
   M.r = c.take<double>(nv);
-  M.z = c.take<double>(nv);
   M.p = c.take<double>(nv);
   M.q = c.take<double>(nv);
   M.bt = c.take<double>(nv);
-  M.zold = c.take<double>(nv);
   M.r32 = c.take<float>(nv);
   M.z32 = c.take<float>(nv);
+  M.z32old = c.take<float>(nv);
   M.scal = c.take<double>((size_t)R * S_COUNT);
   M.partial = c.take<double>((size_t)2 * M.G * R);
   M.tc_err = c.take<int>(1);
@@ -479,19 +582,41 @@ namespace {
 
 inline unsigned threads_for(int R) { return (unsigned)(((R + 31) / 32) * 32); }
 
-// mr_bsr_kernel with a right-hand-side tile of tx columns and br block rows per CTA
-template <typename TA, typename TV, typename TC, int NP, int MODE>
-void mr_bsr_launch(int tx, int br, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
-                   const TV* b, TV* y, TC omega, cudaStream_t s) {
-  const dim3 grid((unsigned)((n + br - 1) / br), (unsigned)((R + tx - 1) / tx)), block((unsigned)tx, (unsigned)br);
-  if (br >= 4) mr_bsr_kernel<TA, TV, TC, NP, MODE, 4><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
-  else if (br == 2) mr_bsr_kernel<TA, TV, TC, NP, MODE, 2><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
-  else mr_bsr_kernel<TA, TV, TC, NP, MODE, 1><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
+// threads per CTA that a kernel's register use allows (cached per instance)
+template <typename Kern>
+int max_threads_of(Kern k) {
+  cudaFuncAttributes a{};
+  return cudaFuncGetAttributes(&a, (const void*)k) == cudaSuccess ? a.maxThreadsPerBlock : 256;
+}
+
+template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
+void mr_bsr_launch_c(int tx, int br, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
+                     const TV* b, TV* y, TC omega, cudaStream_t s) {
+  static const int mt = max_threads_of(mr_bsr_kernel<TA, TV, TC, NP, MODE, C>);
+  br = std::min(std::max(br, 1), kMrMaxBR);
+  // a CTA larger than the register file allows runs as fewer block rows, then
+  // narrower tiles: the same columns in the same order, so the same results
+  while (tx * br > mt && br > 1) br /= 2;
+  while (tx * br > mt && tx > 32) tx /= 2;
+  const dim3 grid((unsigned)((n + br - 1) / br), (unsigned)((R + tx * C - 1) / (tx * C))),
+      block((unsigned)tx, (unsigned)br);
+  mr_bsr_kernel<TA, TV, TC, NP, MODE, C><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
   count_launch();
+}
+
+// mr_bsr_kernel with tx threads across the right-hand sides, rc columns per
+// thread (a tile of tx rc columns) and br block rows per CTA
+template <typename TA, typename TV, typename TC, int NP, int MODE>
+void mr_bsr_launch(int tx, int br, int rc, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
+                   const TV* b, TV* y, TC omega, cudaStream_t s) {
+  if (rc >= 4) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 4>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
+  else if (rc == 2) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 2>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
+  else mr_bsr_launch_c<TA, TV, TC, NP, MODE, 1>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
 }
 
 inline int tile_of(const MR& M, int l, int mode) { return M.tile[l][mode] ? M.tile[l][mode] : (int)threads_for(M.R); }
 inline int rows_of(const MR& M, int l, int mode) { return M.rows[l][mode] ? M.rows[l][mode] : 1; }
+inline int cols_of(const MR& M, int l, int mode) { return M.cols[l][mode] ? M.cols[l][mode] : 1; }
 
 template <typename TA>
 bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, float* z0, cudaStream_t s) {
@@ -503,12 +628,12 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
     const int n = D.lev[l].n;
     if (mode == 3 && M.tc)
       return mr_tc_smooth(np, n, R, rp, cl, A, x, b, y, w, M.tc_err, D.wait_limit, s);
-    const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode);
+    const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode), rc = cols_of(M, l, mode);
     MR_NP_DISPATCH(np, {
       if (mode == 1)
-        mr_bsr_launch<float, float, float, NP, 1>(tx, br, n, R, rp, cl, (const float*)A, x, b, y, w, s);
+        mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, n, R, rp, cl, (const float*)A, x, b, y, w, s);
       else
-        mr_bsr_launch<TA, float, float, NP, 3>(tx, br, n, R, rp, cl, (const TA*)A, x, b, y, w, s);
+        mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, n, R, rp, cl, (const TA*)A, x, b, y, w, s);
     });
     return true;
   };
@@ -583,9 +708,9 @@ bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t 
   if (M.oz)
     return oz_apply(D.np, L0.n, M.R, L0.rowptr, L0.col, M.oz_img, M.oz_eA, M.oz_xs, M.oz_maxb, x, y, M.tc_err,
                     D.wait_limit, s);
-  const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0);
-  MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, L0.n, M.R, L0.rowptr, L0.col, L0.A, x,
-                                                                     (const double*)nullptr, y, 0.0, s)));
+  const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0), rc = cols_of(M, 0, 0);
+  MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, L0.n, M.R, L0.rowptr, L0.col, L0.A,
+                                                                     x, (const double*)nullptr, y, 0.0, s)));
   return true;
 }
 
@@ -602,15 +727,19 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return false;
   auto pick = [&](int l, int mode, auto&& launch_one) {
     float tbest = 3.0e38f;
-    for (int tx = 32; tx <= 1024; tx *= 2) {
-      if (tx > tmax && tx != 32) break;
-      for (int br : {1, 2, 4}) {
-        if (tx * br > 1024) continue;
-        const float t = time_calls(s, e0, e1, 2, [&] { launch_one(tx, br); });
-        if (t < tbest) {
-          tbest = t;
-          M.tile[l][mode] = tx;
-          M.rows[l][mode] = br;
+    for (int rc : {1, 2, 4}) {
+      for (int tx = 32; tx <= 1024; tx *= 2) {
+        if (tx * rc > tmax && tx != 32) break;
+        if (rc > 1 && tx * rc > tmax) break;   // a thread's extra columns would all be padding
+        for (int br : {1, 2, 4}) {
+          if (tx * br > 1024) continue;
+          const float t = time_calls(s, e0, e1, 2, [&] { launch_one(tx, br, rc); });
+          if (t < tbest) {
+            tbest = t;
+            M.tile[l][mode] = tx;
+            M.rows[l][mode] = br;
+            M.cols[l][mode] = rc;
+          }
         }
       }
     }
@@ -620,8 +749,8 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
     const DevLevel& L0 = D.lev[0];
     const size_t nv = (size_t)L0.n * np * R;
     cudaMemsetAsync(M.p, 0, nv * sizeof(double), s);
-    pick(0, 0, [&](int tx, int br) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, L0.n, R, L0.rowptr, L0.col, L0.A,
+    pick(0, 0, [&](int tx, int br, int rc) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, L0.n, R, L0.rowptr, L0.col, L0.A,
                                                                          (const double*)M.p, (const double*)nullptr,
                                                                          M.q, 0.0, s)));
     });
@@ -632,13 +761,13 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
     MRLevel& L = M.lev[l];
     const size_t nv = (size_t)DL.n * np * R;
     for (float* v : {L.x, L.b, L.bh, L.t}) cudaMemsetAsync(v, 0, nv * sizeof(float), s);
-    pick(l, 1, [&](int tx, int br) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<float, float, float, NP, 1>(tx, br, DL.n, R, DL.rowptr, DL.col,
+    pick(l, 1, [&](int tx, int br, int rc) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, DL.n, R, DL.rowptr, DL.col,
                                                                       (const float*)L.A, (const float*)L.x,
                                                                       (const float*)L.b, L.t, w, s)));
     });
-    pick(l, 3, [&](int tx, int br) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<TA, float, float, NP, 3>(tx, br, DL.n, R, DL.hrowptr, DL.hcol,
+    pick(l, 3, [&](int tx, int br, int rc) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, DL.n, R, DL.hrowptr, DL.hcol,
                                                                    (const TA*)L.Ahat, (const float*)L.x,
                                                                    (const float*)L.bh, L.t, w, s)));
     });
@@ -650,13 +779,17 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
   return ok;
 }
 
-void mr_dot(DeviceState& D, MR& M, const double* x, const double* y, const double* w, int which, double tol,
-            cudaStream_t s) {
+void mr_finalize(MR& M, int which, bool flexible, double tol, cudaStream_t s) {
+  mr_finalize_kernel<<<(M.R + 127) / 128, 128, 0, s>>>(M.R, M.G, M.partial, which, flexible ? 1 : 0, tol, M.scal);
+  count_launch();
+}
+
+template <typename TY>
+void mr_dot(DeviceState& D, MR& M, const double* x, const TY* y, const TY* w, int which, double tol, cudaStream_t s) {
   const int nrows = (int)(D.ne * D.np);
   const unsigned T = threads_for(M.R);
-  mr_dot_kernel<<<M.G, T, 0, s>>>(nrows, M.R, M.G, x, y, w, M.partial);
-  mr_finalize_kernel<<<(M.R + 127) / 128, 128, 0, s>>>(M.R, M.G, M.partial, which, w != nullptr, tol, M.scal);
-  count_launch(2);
+  mr_dot_kernel<TY><<<M.G, T, 0, s>>>(nrows, M.R, M.G, x, y, w, M.partial);
+  mr_finalize(M, which, w != nullptr, tol, s);
 }
 
 }  // namespace
@@ -699,15 +832,12 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
   count_launch();
   cudaMemsetAsync(M.x, 0, sizeof(double) * nv, s);
   cudaMemcpyAsync(M.r, M.bt, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
-  mr_dot(D, M, M.bt, M.bt, nullptr, 3, o.tol, s);
-  mr_dot(D, M, M.r, M.r, nullptr, 4, o.tol, s);
+  mr_dot<double>(D, M, M.bt, M.bt, nullptr, 3, o.tol, s);
+  mr_dot<double>(D, M, M.r, M.r, nullptr, 4, o.tol, s);
+  // the V-cycle maps r32 (FP32 copy of r, written by mr_update_kernel after the
+  // first step) to z32; z = z32 widened exactly, so the FP64 steps read z32
   auto precond = [&]() -> bool {
-    mr_convert_kernel<double, float><<<gv, 256, 0, s>>>(nv, M.r, M.r32);
-    const bool r2 = M.bf16 ? mr_vcycle<__nv_bfloat16>(D, M, o, M.r32, M.z32, s)
-                           : mr_vcycle<float>(D, M, o, M.r32, M.z32, s);
-    mr_convert_kernel<float, double><<<gv, 256, 0, s>>>(nv, M.z32, M.z);
-    count_launch(2);
-    return r2;
+    return M.bf16 ? mr_vcycle<__nv_bfloat16>(D, M, o, M.r32, M.z32, s) : mr_vcycle<float>(D, M, o, M.r32, M.z32, s);
   };
   std::vector<double> hs((size_t)R * S_COUNT);
   cudaMemcpyAsync(hs.data(), M.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
@@ -732,9 +862,11 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
     }
   }
   if (ndone < R) {
+    mr_convert_kernel<double, float><<<gv, 256, 0, s>>>(nv, M.r, M.r32);
+    count_launch();
     ok = precond();
-    mr_dot(D, M, M.r, M.z, nullptr, 2, o.tol, s);
-    mr_p_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, 1, M.z, M.p);
+    mr_dot<float>(D, M, M.r, M.z32, nullptr, 2, o.tol, s);
+    mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 1, M.z32, M.p);
     count_launch();
     while (ok) {
       if (it >= o.maxit) {
@@ -742,10 +874,10 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
         break;
       }
       ok = mr_apply64(D, M, M.p, M.q, s);
-      mr_dot(D, M, M.p, M.q, nullptr, 0, o.tol, s);
-      mr_update_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, M.p, M.q, M.x, M.r);
+      mr_dot<double>(D, M, M.p, M.q, nullptr, 0, o.tol, s);
+      mr_update_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, M.p, M.q, M.x, M.r, M.r32, M.partial);
       count_launch();
-      mr_dot(D, M, M.r, M.r, nullptr, 1, o.tol, s);
+      mr_finalize(M, 1, false, o.tol, s);
       cudaMemcpyAsync(hs.data(), M.scal, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
       int tc_err_it = 0;
       if (M.tc || M.oz) cudaMemcpyAsync(&tc_err_it, M.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -771,10 +903,10 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
         }
       }
       if (ndone == R) break;
-      cudaMemcpyAsync(M.zold, M.z, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+      std::swap(M.z32, M.z32old);
       ok = precond();
-      mr_dot(D, M, M.r, M.z, M.zold, 2, o.tol, s);
-      mr_p_kernel<<<gv, 256, 0, s>>>(nrows, R, M.scal, 0, M.z, M.p);
+      mr_dot<float>(D, M, M.r, M.z32, M.z32old, 2, o.tol, s);
+      mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 0, M.z32, M.p);
       count_launch();
     }
   }
