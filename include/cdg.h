@@ -374,6 +374,17 @@ int cdg_set_wait_limit(cdg_handle* h, int32_t limit);
  * CDG_ECUDA. */
 int cdg_fp64_fma_probe(int32_t blocks, int64_t iters, double* sink, void* stream);
 
+/* Element-wise conversion of a device vector between binary64 and binary32
+ * (no counterpart in the paper: the conversion the mixed-precision solves
+ * apply at the edges of their FP32 V-cycle, Section 4.3 being run in two
+ * precisions).  to_fp32 = 1: in is n doubles, out n floats, rounded to
+ * nearest with ties to even; to_fp32 = 0: in is n floats, out n doubles
+ * (exact).  The kernels build the results from the IEEE 754 bit fields with
+ * integer operations; results equal the IEEE conversions for every input
+ * (NaN payloads aside).  Asynchronous on `stream`.  Errors: CDG_EINVAL (NULL
+ * pointer with n > 0, n < 0), CDG_ECUDA. */
+int cdg_convert(const void* in, void* out, int64_t n, int32_t to_fp32, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (instrumentation for benchmarks; thread-safe, never reset). */
 int64_t cdg_kernel_launches(void);

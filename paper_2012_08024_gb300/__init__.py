@@ -77,6 +77,7 @@ SIGNATURES = {
     "cdg_set_wait_limit": (_I32, [_P, _I32]),
     "cdg_apply_multi": (_I32, [_P, _P, _P, _P]),
     "cdg_fp64_fma_probe": (_I32, [_I32, _I64, _P, _P]),
+    "cdg_convert": (_I32, [_P, _P, _I64, _I32, _P]),
     "cdg_rhs": (_I32, [_P, _P, _P, _P, _P, _P]),
     "cdg_solve": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P]),
     "cdg_solve_b": (_I32, [_P, _P, _P, _I32, _P, _P, _P]),
@@ -116,6 +117,22 @@ def lib():
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().cdg_kernel_launches())
+
+
+def convert(x, stream=None):
+    """binary64 <-> binary32 conversion of a CUDA tensor by the library's
+    kernel (cdg_convert): float64 in -> float32 out (round to nearest even),
+    float32 in -> float64 out (exact)."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype not in (torch.float64, torch.float32):
+        raise ValueError("convert: a float64 or float32 CUDA tensor is required")
+    x = x.contiguous()
+    to32 = x.dtype == torch.float64
+    out = torch.empty(x.shape, dtype=torch.float32 if to32 else torch.float64, device=x.device)
+    rc = lib().cdg_convert(_ptr(x), _ptr(out), x.numel(), int(to32), _stream_ptr(stream))
+    if rc:
+        raise CdgError(rc, "cdg_convert failed")
+    return out
 
 
 def _dvec(t, n: int, name: str, dtype: str = "float64") -> int | None:

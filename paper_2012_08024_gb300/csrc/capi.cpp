@@ -491,6 +491,11 @@ int cdg_fp64_fma_probe(int32_t blocks, int64_t iters, double* sink, void* stream
   return dev_fma_probe(blocks, iters, sink, stream);
 }
 
+int cdg_convert(const void* in, void* out, int64_t n, int32_t to_fp32, void* stream) {
+  if (n < 0 || (n > 0 && (!in || !out))) return CDG_EINVAL;
+  return dev_convert(in, out, (long long)n, to_fp32 ? 1 : 0, stream);
+}
+
 int cdg_rhs(cdg_handle* h, const double* f_q, const double* gD, const double* gN, double* b, void* stream) {
   if (!h || !f_q || !b) return h ? fail(h, CDG_EINVAL, "NULL argument") : CDG_EINVAL;
   return nothrow(h, [&] { return dev_rhs(h, f_q, gD, gN, b, true, stream); });

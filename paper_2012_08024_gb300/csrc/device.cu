@@ -27,6 +27,7 @@ void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relax
 long long launch_count() { return g_launches.load(); }
 
 namespace {
+using cdgk::cvt;
 using cdgk::ldg;
 using cdgk::row_acc;
 using cdgk::VecLoad;
@@ -448,9 +449,9 @@ __global__ void coarse_kernel(int nc, const int* __restrict__ crow_seg, const in
   const double* a = Ainv + cinv_off[m] + (size_t)(row - r0) * nm;
   const TI* bm = b + r0;
   double s = 0.0;
-  for (int j = lane; j < nm; j += 32) s = fma(a[j], (double)bm[j], s);
+  for (int j = lane; j < nm; j += 32) s = fma(a[j], cvt<double>(bm[j]), s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = ADD ? (TO)((double)x[row] + s) : (TO)s;
+  if (lane == 0) x[row] = ADD ? cvt<TO>(cvt<double>(x[row]) + s) : cvt<TO>(s);
 }
 
 // Between two degrees of the p-multigrid levels (Section 4.4) the orthonormal
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) ptrunc_prolong_kernel(int n, int npf
 template <typename TI, typename TO>
 __global__ void convert_kernel(size_t n, const TI* __restrict__ a, TO* __restrict__ b) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (TO)a[i];
+    b[i] = cvt<TO>(a[i]);
 }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -1702,6 +1703,16 @@ int dev_fma_probe(int blocks, long long iters, double* sink, void* stream) {
   // 16 chains of iters / 2 steps: the same FMA count as 8 chains of iters steps
   launch(fma64_probe_kernel<16>, (unsigned)blocks, kThreads, (cudaStream_t)stream, (iters + 1) / 2, 0.5,
          0.9999999, 1e-7, sink);
+  return cudaGetLastError() == cudaSuccess ? CDG_OK : CDG_ECUDA;
+}
+
+int dev_convert(const void* in, void* out, long long n, int to_fp32, void* stream) {
+  if (n == 0) return CDG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (to_fp32)
+    launch(convert_kernel<double, float>, vec_grid((size_t)n), kThreads, s, (size_t)n, (const double*)in, (float*)out);
+  else
+    launch(convert_kernel<float, double>, vec_grid((size_t)n), kThreads, s, (size_t)n, (const float*)in, (double*)out);
   return cudaGetLastError() == cudaSuccess ? CDG_OK : CDG_ECUDA;
 }
 

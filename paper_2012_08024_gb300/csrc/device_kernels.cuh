@@ -9,6 +9,56 @@ namespace cdgk {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Conversions between binary32 and binary64 built from the IEEE 754 bit
+// fields with integer operations.  On this GPU a conversion instruction to or
+// from FP64 runs at the rate of the FP64 pipe (about two per clock per SM),
+// as slow as an FP64 FMA; the vector kernels of the FP64 CG would spend as
+// much time converting as computing.  Both functions give the correctly
+// rounded IEEE result; the cases outside the common range (zero is handled
+// here; subnormals, infinities and NaN) fall back to the conversion
+// instruction.
+//
+// binary32 -> binary64 is exact: sign, exponent rebiased by 1023 - 127,
+// the 23 fraction bits placed at the top of the 52.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e - 1u < 0xFEu)   // 1 <= e <= 254: a normal number
+    return __longlong_as_double(
+        (long long)(sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);   // +-0
+  return (double)f;
+}
+
+// binary64 -> binary32, round to nearest, ties to even: for a result in the
+// normal binary32 range keep the top 23 fraction bits and add one unit when
+// the 29 dropped bits exceed half a unit, or equal it with an odd kept part.
+// The carry of that addition moves into the exponent field as it should, and
+// from the largest finite value into the infinity encoding.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e >= -126 && e <= 127) {
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const unsigned int kept = (unsigned int)(m >> 29);
+    const unsigned int rest = (unsigned int)(m & 0x1FFFFFFFull);
+    unsigned int r = ((unsigned int)(e + 127) << 23) | kept;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (kept & 1u))) r += 1u;
+    return __uint_as_float(sgn | r);
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(sgn);   // +-0
+  return (float)d;
+}
+
+template <typename TO, typename TI>
+__device__ __forceinline__ TO cvt(TI v) {
+  if constexpr (sizeof(TO) == 8 && sizeof(TI) == 4) return f32_to_f64(v);
+  else if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8) return f64_to_f32(v);
+  else return (TO)v;
+}
+
 // NP consecutive values of x as aligned vector loads; CG: through L2 only
 // (ld.global.cg: coherent within a kernel whose own phases write x), else
 // through the read-only path

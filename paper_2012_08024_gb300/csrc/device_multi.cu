@@ -16,9 +16,14 @@
 #include <string>
 #include <vector>
 
+#include "device_kernels.cuh"
 #include "device_state.h"
 
 namespace {
+
+using cdgk::cvt;
+using cdgk::f32_to_f64;
+using cdgk::f64_to_f32;
 
 template <typename T>
 struct Conv;
@@ -193,22 +198,35 @@ __global__ void mr_prolong_kernel(int R, const int* __restrict__ parent, const T
 }
 
 // coarsest (one mesh): x[row][r] = sum_j Ainv[row][j] b[j][r], FP64 accumulation
-template <typename TV>
+// in ascending j; a CTA owns CR consecutive rows and thread r one column, so
+// each b value is widened once per CR rows
+constexpr int kCoarseRows = 4;
+
+template <typename TV, int CR>
 __global__ void mr_coarse_kernel(int nc, int R, const double* __restrict__ Ainv, const TV* __restrict__ b,
                                  TV* __restrict__ x) {
-  const int row = blockIdx.x;
+  const int row0 = blockIdx.x * CR;
   const int r = threadIdx.x;
   if (r >= R) return;
-  const double* a = Ainv + (size_t)row * nc;
-  double s = 0.0;
-  for (int j = 0; j < nc; ++j) s = fma(a[j], (double)b[(size_t)j * R + r], s);
-  x[(size_t)row * R + r] = (TV)s;
+  const int nr = min(CR, nc - row0);
+  double s[CR];
+#pragma unroll
+  for (int q = 0; q < CR; ++q) s[q] = 0.0;
+  for (int j = 0; j < nc; ++j) {
+    const double bv = cvt<double>(b[(size_t)j * R + r]);
+#pragma unroll
+    for (int q = 0; q < CR; ++q)
+      if (q < nr) s[q] = fma(Ainv[(size_t)(row0 + q) * nc + j], bv, s[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < CR; ++q)
+    if (q < nr) x[(size_t)(row0 + q) * R + r] = cvt<TV>(s[q]);
 }
 
 template <typename TI, typename TO>
 __global__ void mr_convert_kernel(size_t n, const TI* __restrict__ a, TO* __restrict__ b) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (TO)a[i];
+    b[i] = cvt<TO>(a[i]);
 }
 
 // The per-column vector kernels of the outer CG share one partition: CTA g of
@@ -233,24 +251,27 @@ __global__ void mr_dot_kernel(int nrows, int R, int G, const double* __restrict_
   double s = 0.0, s2 = 0.0;
   int row = lo;
   for (; row + 4 <= hi; row += 4) {
-    double xv[4], yv[4], wv[4];
+    // all loads of the group first (raw words), conversions after: a
+    // conversion's branch between two loads would keep them from overlapping
+    double xv[4];
+    TY yv[4], wv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const size_t o = (size_t)(row + u) * R + r;
       xv[u] = x[o];
-      yv[u] = (double)y[o];
-      wv[u] = w ? (double)w[o] : 0.0;
+      yv[u] = y[o];
+      wv[u] = w ? w[o] : TY(0);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      s = fma(xv[u], yv[u], s);
-      if (w) s2 = fma(xv[u], wv[u], s2);
+      s = fma(xv[u], cvt<double>(yv[u]), s);
+      if (w) s2 = fma(xv[u], cvt<double>(wv[u]), s2);
     }
   }
   for (; row < hi; ++row) {
     const size_t o = (size_t)row * R + r;
-    s = fma(x[o], (double)y[o], s);
-    if (w) s2 = fma(x[o], (double)w[o], s2);
+    s = fma(x[o], cvt<double>(y[o]), s);
+    if (w) s2 = fma(x[o], cvt<double>(w[o]), s2);
   }
   partial[(size_t)g * R + r] = s;
   if (w) partial[(size_t)(G + g) * R + r] = s2;
@@ -324,7 +345,7 @@ __global__ void mr_update_kernel(int nrows, int R, int G, const double* __restri
       x[o] = fma(a, pv[u], xv[u]);
       const double v = fma(-a, qv[u], rv[u]);
       res[o] = v;
-      r32[o] = (float)v;
+      r32[o] = f64_to_f32(v);
       s = fma(v, v, s);
     }
   }
@@ -333,7 +354,7 @@ __global__ void mr_update_kernel(int nrows, int R, int G, const double* __restri
     x[o] = fma(a, p[o], x[o]);
     const double v = fma(-a, q[o], res[o]);
     res[o] = v;
-    r32[o] = (float)v;
+    r32[o] = f64_to_f32(v);
     s = fma(v, v, s);
   }
   partial[(size_t)g * R + r] = s;
@@ -349,19 +370,24 @@ __global__ void mr_p_kernel(int nrows, int R, int G, const double* __restrict__ 
   const double beta = first ? 0.0 : scal[(size_t)r * S_COUNT + S_BETA];
   int row = lo;
   for (; row + 4 <= hi; row += 4) {
-    double zv[4], pv[4];
+    float zv[4];   // raw words first, conversions after (see mr_dot_kernel)
+    double pv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const size_t o = (size_t)(row + u) * R + r;
-      zv[u] = (double)z[o];
+      zv[u] = z[o];
       pv[u] = first ? 0.0 : p[o];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) p[(size_t)(row + u) * R + r] = first ? zv[u] : fma(beta, pv[u], zv[u]);
+    for (int u = 0; u < 4; ++u) {
+      const double zo = f32_to_f64(zv[u]);
+      p[(size_t)(row + u) * R + r] = first ? zo : fma(beta, pv[u], zo);
+    }
   }
   for (; row < hi; ++row) {
     const size_t o = (size_t)row * R + r;
-    p[o] = first ? (double)z[o] : fma(beta, p[o], (double)z[o]);
+    const double zo = f32_to_f64(z[o]);
+    p[o] = first ? zo : fma(beta, p[o], zo);
   }
 }
 
@@ -638,7 +664,8 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
     return true;
   };
   if (nlev == 1) {
-    mr_coarse_kernel<float><<<D.nc, T, 0, s>>>(D.nc, R, D.coarse_inv, b0, z0);
+    mr_coarse_kernel<float, kCoarseRows><<<(D.nc + kCoarseRows - 1) / kCoarseRows, T, 0, s>>>(D.nc, R, D.coarse_inv,
+                                                                                            b0, z0);
     count_launch();
     return true;
   }
@@ -672,7 +699,8 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
       count_launch(2);
     }
   }
-  mr_coarse_kernel<float><<<D.nc, T, 0, s>>>(D.nc, R, D.coarse_inv, M.lev[nlev - 1].b, M.lev[nlev - 1].x);
+  mr_coarse_kernel<float, kCoarseRows><<<(D.nc + kCoarseRows - 1) / kCoarseRows, T, 0, s>>>(
+      D.nc, R, D.coarse_inv, M.lev[nlev - 1].b, M.lev[nlev - 1].x);
   count_launch();
   for (int l = nlev - 2; l >= 0; --l) {
     MRLevel& L = M.lev[l];

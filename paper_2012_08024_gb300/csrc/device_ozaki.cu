@@ -23,12 +23,13 @@
 // K-major SWIZZLE_NONE core matrices: 8 rows x 16 bytes, LBO = 128 bytes
 // along K, SBO = 256 bytes between 8-row groups); X is sliced once per apply
 // into the same images, 4 KB per (element, column tile, slice), and staged per
-// block as S operands A = X_J^T (128 columns x 16).  One CTA of 128 threads
-// owns a tile of 128 columns; one thread copies the operands of a block into a
-// ring of three shared-memory stages with bulk copies, issues its MMAs and
-// commits them to the stage's mbarrier, so the copies of the next blocks
-// overlap the MMAs of the current one.  Every wait has an iteration limit;
-// on expiry the kernel sets the error flag, drains its MMAs (default limit),
+// block as S operands A = X_J^T (128 columns x 16).  A CTA owns a tile of 128
+// columns: one thread copies the operands of each block into a ring of three
+// shared-memory stages with bulk copies and issues its MMAs, so the copies of
+// the next blocks overlap the MMAs of the current one, and four epilogue warps
+// read finished rows from one of two TMEM accumulator sets while the MMAs of
+// the next row fill the other.  Every wait has an iteration limit; on expiry
+// the kernel sets the error flag, drains its copies and MMAs (default limit),
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -53,7 +54,10 @@ constexpr int kABytes = kBRows * 16 * 2;      // all A slices of one block: 4 KB
 constexpr int kStageBytes = kS * kXBytes + kABytes;
 constexpr int kStages = 3;
 constexpr int kWaitLimit = 1 << 22;
-constexpr int kTmemCols = 16 * kS;            // accumulators d = 0 .. S-1, 16 columns each
+constexpr int kAccSets = 2;                   // accumulator sets: rows in flight between MMAs and epilogue
+constexpr int kTmemCols = 16 * kS * kAccSets;  // per set, accumulators d = 0 .. S-1, 16 columns each
+constexpr int kEpiThreads = kTile;            // epilogue warps 0-3: one column of the tile per thread
+constexpr int kOzThreads = kEpiThreads + 32;    // and warp 4, whose lane 0 copies and issues the MMAs
 
 __host__ __device__ __forceinline__ int kmaj16(int row, int k) {
   return (row >> 3) * (int)kSBO + (k >> 3) * (int)kLBO + (row & 7) * 16 + (k & 7) * 2;
@@ -180,35 +184,64 @@ __device__ __forceinline__ void arrive_expect(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// CTA (x, c) owns the block rows K = x, x + gridDim.x, ... and column tile c.
-// Thread 0 streams the blocks of those rows through a ring of kStages shared
-// memory stages: for each block it waits until the stage is free (the MMAs
-// that read it completed: empty[]), posts the expected bytes and two bulk
-// copies (the 32 KB X_J slice images and the block's 4 KB slice image) on
-// full[], and, kStages - 1 blocks later, waits on full[] and issues the
-// block's S MMAs, committed to empty[].  At the end of a row it commits to
-// rowbar; all threads wait there and run the epilogue.
+// A bounded wait that also gives up once another role of the CTA has failed
+__device__ __forceinline__ bool wait_or_fail(uint32_t mbar, uint32_t parity, int limit, const volatile int* fail) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (!done && *fail) return false;
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+
+// CTA (x, c) owns the block rows K = x, x + gridDim.x, ... and column tile c,
+// with two roles that run concurrently:
+//  - lane 0 of warp 4 streams the blocks of those rows through a ring of
+//    kStages shared-memory stages (a stage is free once the MMAs that read it
+//    completed: empty[]; its bulk copies complete full[]) and issues each
+//    block's S MMAs into accumulator set a = (row index) mod 2 of TMEM, then
+//    commits the row to accf[a].  Before the first MMA of a row it waits on
+//    acce[a], until the epilogue has read that set's previous row.
+//  - warps 0-3 (lane = column of the tile) wait on accf[a], read the row's S
+//    accumulators, release the set (acce[a], one arrive per warp), combine
+//    them exactly and write y.
+// So the MMAs of row k + 1 run while the epilogue of row k converts and
+// stores.  Every wait is bounded; a role that gives up sets the shared fail
+// flag, on which the other role's waits give up too.  Before the CTA ends the
+// issuing thread waits (default limit) for its copies in flight and for all of
+// its MMAs (a final commit), and warp 0 frees the tensor memory.
 template <int NP>
-__global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, int tiles, const int* __restrict__ rowptr,
-                                                         const int* __restrict__ col,
-                                                         const unsigned char* __restrict__ Aimg,
-                                                         const int* __restrict__ eA,
-                                                         const unsigned char* __restrict__ xs,
-                                                         const int* __restrict__ maxb, double* __restrict__ y,
-                                                         int* __restrict__ err, int wait_limit) {
+__global__ void __launch_bounds__(kOzThreads, 2) oz_apply_kernel(int n, int R, int tiles,
+                                                               const int* __restrict__ rowptr,
+                                                               const int* __restrict__ col,
+                                                               const unsigned char* __restrict__ Aimg,
+                                                               const int* __restrict__ eA,
+                                                               const unsigned char* __restrict__ xs,
+                                                               const int* __restrict__ maxb, double* __restrict__ y,
+                                                               int* __restrict__ err, int wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], rowbar;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAccSets], acce[kAccSets], fin;
   __shared__ uint32_t tmem_base;
-  __shared__ int fail_s;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ volatile int fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.y;
-  const int r = c * kTile + tid;   // this thread's column
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&rowbar)));
+    for (int a = 0; a < kAccSets; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[a])), "n"(kEpiThreads / 32));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     fail_s = 0;
   }
@@ -221,128 +254,144 @@ __global__ void __launch_bounds__(kTile) oz_apply_kernel(int n, int R, int tiles
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int ex = r < R ? maxb[r] - 1022 : 0;   // E_X of this column
-  // producer cursor (thread 0): the next block to copy, as (row, block)
-  int pk = blockIdx.x, pb = pk < n ? rowptr[pk] : 0;
-  long long issued = 0, consumed = 0;   // blocks copied / blocks whose MMAs are issued
-  int rows_done = 0;                    // rowbar waits made by every thread
-  int rb_commits = 0, rb_seen = 0;      // thread 0: rowbar commits, and phases it saw complete
-  bool ok = true;
-  auto advance = [&]() {   // the producer cursor to the next block of this CTA's rows
-    while (pk < n && pb >= rowptr[pk + 1]) {
-      pk += gridDim.x;
-      pb = pk < n ? rowptr[pk] : 0;
-    }
-  };
-  auto issue = [&]() -> bool {   // copies of the block at the cursor into stage issued % kStages
-    advance();
-    if (pk >= n) return true;
-    const int st = (int)(issued % kStages);
-    if (issued >= kStages &&
-        !wait_phase(smem_u32(&empty[st]), (uint32_t)(((issued / kStages) - 1) & 1), wait_limit))
-      return false;
-    unsigned char* sx = smem + st * kStageBytes;
-    const uint32_t fb = smem_u32(&full[st]);
-    arrive_expect(fb, (uint32_t)kStageBytes);
-    bulk_g2s(sx, xs + ((size_t)col[pb] * tiles + c) * kS * (size_t)kXBytes, (uint32_t)(kS * kXBytes), fb);
-    bulk_g2s(sx + kS * kXBytes, Aimg + (size_t)pb * kABytes, (uint32_t)kABytes, fb);
-    ++issued;
-    ++pb;
-    return true;
-  };
-  for (int K = blockIdx.x; K < n; K += gridDim.x) {
-    const int b0 = rowptr[K], b1 = rowptr[K + 1];
-    if (tid == 0 && ok) {
-      for (int bb = b0; bb < b1 && ok; ++bb) {
-        while (ok && issued < consumed + kStages) {
-          const long long before = issued;
-          ok = issue();
-          if (issued == before) break;   // no block left to copy
+  if (warp == kEpiThreads / 32) {
+    if (lane == 0) {
+      // ---- copies and MMAs
+      int pk = blockIdx.x, pb = pk < n ? rowptr[pk] : 0;   // the next block to copy, as (row, block)
+      long long issued = 0, consumed = 0;                 // blocks copied / blocks whose MMAs are issued
+      bool ok = true;
+      auto advance = [&]() {
+        while (pk < n && pb >= rowptr[pk + 1]) {
+          pk += gridDim.x;
+          pb = pk < n ? rowptr[pk] : 0;
         }
-        if (!ok) break;
-        const int st = (int)(consumed % kStages);
-        if (!wait_phase(smem_u32(&full[st]), (uint32_t)((consumed / kStages) & 1), wait_limit)) {
+      };
+      auto issue = [&]() -> bool {   // copies of the block at the cursor into stage issued % kStages
+        advance();
+        if (pk >= n) return true;
+        const int st = (int)(issued % kStages);
+        if (issued >= kStages &&
+            !wait_or_fail(smem_u32(&empty[st]), (uint32_t)(((issued / kStages) - 1) & 1), wait_limit, &fail_s))
+          return false;
+        unsigned char* sx = smem + st * kStageBytes;
+        const uint32_t fb = smem_u32(&full[st]);
+        arrive_expect(fb, (uint32_t)kStageBytes);
+        bulk_g2s(sx, xs + ((size_t)col[pb] * tiles + c) * kS * (size_t)kXBytes, (uint32_t)(kS * kXBytes), fb);
+        bulk_g2s(sx + kS * kXBytes, Aimg + (size_t)pb * kABytes, (uint32_t)kABytes, fb);
+        ++issued;
+        ++pb;
+        return true;
+      };
+      int rowi = 0;   // rows of this CTA with blocks, so far
+      for (int K = blockIdx.x; K < n && ok; K += gridDim.x) {
+        const int b0 = rowptr[K], b1 = rowptr[K + 1];
+        if (b1 == b0) continue;
+        const int a = rowi % kAccSets;
+        if (rowi >= kAccSets &&
+            !wait_or_fail(smem_u32(&acce[a]), (uint32_t)(((rowi / kAccSets) - 1) & 1), wait_limit, &fail_s)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        unsigned char* sx = smem + st * kStageBytes;
-        const uint64_t bdesc = smem_desc(smem_u32(sx + kS * kXBytes));
+        const uint32_t dacc = tmem + (uint32_t)(a * 16 * kS);
+        for (int bb = b0; bb < b1 && ok; ++bb) {
+          while (ok && issued < consumed + kStages) {
+            const long long before = issued;
+            ok = issue();
+            if (issued == before) break;   // no block left to copy
+          }
+          if (!ok) break;
+          const int st = (int)(consumed % kStages);
+          if (!wait_or_fail(smem_u32(&full[st]), (uint32_t)((consumed / kStages) & 1), wait_limit, &fail_s)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          unsigned char* sx = smem + st * kStageBytes;
+          const uint64_t bdesc = smem_desc(smem_u32(sx + kS * kXBytes));
 #pragma unroll
-        for (int t = 0; t < kS; ++t)
-          mma_bf16(tmem + (uint32_t)(16 * t), smem_desc(smem_u32(sx + t * kXBytes)), bdesc, idesc_bf16(16 * (kS - t)),
-                   (bb > b0 || t > 0) ? 1u : 0u);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&empty[st])));
-        ++consumed;
+          for (int t = 0; t < kS; ++t)
+            mma_bf16(dacc + (uint32_t)(16 * t), smem_desc(smem_u32(sx + t * kXBytes)), bdesc,
+                     idesc_bf16(16 * (kS - t)), (bb > b0 || t > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty[st]));
+          ++consumed;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&accf[a]));
+        ++rowi;
       }
-      if (ok && b1 > b0) {
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&rowbar)));
-        ++rb_commits;
+      if (!ok) {
+        fail_s = 1;
+        atomicExch(err, 1);
       }
-      if (!ok) fail_s = 1;
+      // copies in flight land and issued MMAs finish before the CTA ends: every
+      // unconsumed stage phase in order (at most one per stage), then one commit
+      // that completes after all earlier MMAs of this thread
+      for (long long u = consumed; u < issued; ++u)
+        wait_phase(smem_u32(&full[u % kStages]), (uint32_t)((u / kStages) & 1), kWaitLimit);
+      mma_commit(smem_u32(&fin));
+      wait_phase(smem_u32(&fin), 0u, kWaitLimit);
     }
-    __syncthreads();
-    if (fail_s) {
-      ok = false;
-      break;
-    }
-    if (b1 > b0) {
-      if (!wait_phase(smem_u32(&rowbar), (uint32_t)(rows_done & 1), wait_limit)) ok = false;
-      else if (tid == 0) ++rb_seen;
-      ++rows_done;
-    }
-    if (__syncthreads_or(ok ? 0 : 1)) {
-      ok = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: y[K][i][r] = 2^{E_A + E_X - 63} sum_d acc_d 2^{7 (S - 1 - d)}, in two halves of i
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  } else {
+    // ---- epilogue: y[K][i][r] = 2^{E_A + E_X - 63} sum_d acc_d 2^{7 (S - 1 - d)}
+    const int r = c * kTile + tid;   // this thread's column
+    const int ex = r < R ? maxb[r] - 1022 : 0;
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    int rowi = 0;
+    for (int K = blockIdx.x; K < n; K += gridDim.x) {
+      const int b0 = rowptr[K], b1 = rowptr[K + 1];
+      if (b1 == b0) {
+        if (r < R)
+          for (int i = 0; i < NP; ++i) y[((size_t)K * NP + i) * R + r] = 0.0;
+        continue;
+      }
+      const int a = rowi % kAccSets;
+      const bool got = wait_or_fail(smem_u32(&accf[a]), (uint32_t)((rowi / kAccSets) & 1), wait_limit, &fail_s);
+      if (!__all_sync(0xffffffffu, got ? 1 : 0)) {   // the warp leaves together (tcgen05.ld is warp-wide)
+        if (lane == 0) {
+          fail_s = 1;
+          atomicExch(err, 1);
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t taddr = tmem + lanes + (uint32_t)(a * 16 * kS);
+      long long vh[NP], vl[NP];
 #pragma unroll
-    for (int h = 0; h < (NP + 7) / 8; ++h) {
-      uint32_t v[kS][8];
+      for (int h = 0; h < (NP + 7) / 8; ++h) {
+        uint32_t v[kS][8];
 #pragma unroll
-      for (int d = 0; d < kS; ++d)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
-                       "=r"(v[d][6]), "=r"(v[d][7])
-                     : "r"(taddr + (uint32_t)(16 * d + 8 * h)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (r < R) {
+        for (int d = 0; d < kS; ++d)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                         "=r"(v[d][6]), "=r"(v[d][7])
+                       : "r"(taddr + (uint32_t)(16 * d + 8 * h)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int i = 8 * h + q;
           if (i >= NP) break;
-          int a[kS];
+          int s[kS];
 #pragma unroll
-          for (int d = 0; d < kS; ++d) a[d] = b1 > b0 ? __float2int_rz(__uint_as_float(v[d][q])) : 0;
-          const int p0 = a[0] * 128 + a[1], p1 = a[2] * 128 + a[3];
-          const int p2 = a[4] * 128 + a[5], p3 = a[6] * 128 + a[7];
-          const long long vh = (long long)p0 * 16384 + p1, vl = (long long)p2 * 16384 + p3;
-          const int k = eA[(size_t)K * 16 + i] + ex - 63;
-          y[((size_t)K * NP + i) * R + r] = i64_scaled(vh, k + 28) + i64_scaled(vl, k);
+          for (int d = 0; d < kS; ++d) s[d] = __float2int_rz(__uint_as_float(v[d][q]));
+          const int p0 = s[0] * 128 + s[1], p1 = s[2] * 128 + s[3];
+          const int p2 = s[4] * 128 + s[5], p3 = s[6] * 128 + s[7];
+          vh[i] = (long long)p0 * 16384 + p1;
+          vl[i] = (long long)p2 * 16384 + p3;
         }
       }
-    }
-    // the next row's MMAs overwrite the accumulators: every lane has read them
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-  }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(err, 1);
-      // copies in flight land in shared memory and issued MMAs finish before the
-      // CTA ends: wait for both (default limit), every phase in order (a parity
-      // wait two phases behind would not wait)
-      for (long long u = consumed; u < issued; ++u)
-        wait_phase(smem_u32(&full[u % kStages]), (uint32_t)((u / kStages) & 1), kWaitLimit);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&rowbar)));
-      ++rb_commits;
-      for (int ph = rb_seen; ph < rb_commits; ++ph) wait_phase(smem_u32(&rowbar), (uint32_t)(ph & 1), kWaitLimit);
+      // the set is read: the issuing thread may start the row after next in it
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a])) : "memory");
+      if (r < R) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int k = eA[(size_t)K * 16 + i] + ex - 63;
+          y[((size_t)K * NP + i) * R + r] = i64_scaled(vh[i], k + 28) + i64_scaled(vl[i], k);
+        }
+      }
+      ++rowi;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -421,13 +470,13 @@ bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const voi
   oz_colexp_kernel<<<dim3(2 * 152, ty), 256, 0, s>>>(nrows, R, x, maxb);
   const int tiles = (R + kTile - 1) / kTile;
   const int lim = wait_limit < 0 ? kWaitLimit : std::min(wait_limit, kWaitLimit);
-  // two CTAs per SM (108 KB of shared memory, 128 TMEM columns each): the whole grid is resident
+  // two CTAs per SM (108 KB of shared memory, 256 TMEM columns each): the whole grid is resident
   const dim3 grid((unsigned)std::max(1, std::min(n, 152 * 2 / tiles)), (unsigned)tiles);
   const int smem = kStages * kStageBytes;
   auto go = [&](auto slice, auto kern) {
     slice<<<4 * 152 * 4, 256, 0, s>>>(n, R, tiles, x, maxb, (unsigned char*)xs);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, kTile, smem, s>>>(n, R, tiles, rowptr, col, (const unsigned char*)img, eA,
+    kern<<<grid, kOzThreads, smem, s>>>(n, R, tiles, rowptr, col, (const unsigned char*)img, eA,
                                    (const unsigned char*)xs, maxb, y, err, lim);
   };
   switch (np) {

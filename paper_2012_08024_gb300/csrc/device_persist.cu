@@ -24,6 +24,7 @@
 
 namespace {
 
+using cdgk::cvt;
 using cdgk::ldg;
 using cdgk::row_acc;
 
@@ -167,9 +168,9 @@ __device__ void ph_coarse(const PParams& P, const T* b, T* x, bool add) {
     const double* a = P.coarse_inv + P.cinv_off[m] + (size_t)(row - r0) * nm;
     const T* bm = b + r0;
     double s = 0.0;
-    for (int j = lane; j < nm; j += 32) s = fma(ldg(a + j), (double)__ldcg(bm + j), s);
+    for (int j = lane; j < nm; j += 32) s = fma(ldg(a + j), cvt<double>(__ldcg(bm + j)), s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[row] = add ? (T)((double)__ldcg(x + row) + s) : (T)s;
+    if (lane == 0) x[row] = add ? cvt<T>(cvt<double>(__ldcg(x + row)) + s) : cvt<T>(s);
   }
 }
 

@@ -36,5 +36,6 @@ int dev_tuning(const cdg_handle* h, int level, int32_t* out);
 int dev_apply_f32(cdg_handle* h, int level, const float* x, float* y, void* stream);
 int dev_solve_graph(const cdg_handle* h);
 int dev_fma_probe(int blocks, long long iters, double* sink, void* stream);
+int dev_convert(const void* in, void* out, long long n, int to_fp32, void* stream);
 int dev_set_wait_limit(cdg_handle* h, int limit);
 int dev_apply_multi(cdg_handle* h, const double* x, double* y, void* stream);

@@ -137,17 +137,19 @@ def _exported_A0(S):
     return sp.bsr_matrix((ex["val"], ex["col"], ex["rowptr"]), shape=(n * npb, n * npb)).tocsr()
 
 
-@pytest.mark.parametrize("p,R", [(3, 200), (2, 96)])
-def test_tc_fp64_apply_matches_fp64(p, R):
+@pytest.mark.parametrize("p,R,m", [(3, 200, 12), (2, 96, 12), (3, 256, 40)])
+def test_tc_fp64_apply_matches_fp64(p, R, m):
     """The FP64 level-0 apply by exact splitting on tcgen05 (tc_fp64_apply)
     against the library's own A_0 applied in FP64 by scipy, column by column,
     on columns whose scales spread over e^+-6 and a zero column, R spanning a
     full and a ragged 128-column tile: relative error <= 1e-13 per column (the
-    split truncates below 2^-56 of the row and column scales).  The FP64
+    split truncates below 2^-56 of the row and column scales).  On the 40 x 40
+    mesh every CTA runs about ten block rows, so both TMEM accumulator sets
+    and every stage of the copy ring are reused many times.  The FP64
     CUDA-core apply of the same handle type is held to 1e-14."""
     import torch
     from paper_2012_08024_gb300 import Solver
-    mesh = jittered_square(12)
+    mesh = jittered_square(m)
     rng = np.random.default_rng(41)
     for tc in (True, False):
         S = Solver(mesh, p=p, max_levels=3, precision="fp32", nrhs=R, tc_fp64_apply=tc).bind()
@@ -193,9 +195,11 @@ def test_tc_fp64_apply_solve_matches_oracle():
 
 def test_tc_fp64_apply_wait_timeout_is_reported():
     """Failure detection without a fault in the split apply: with the loop-wait
-    limit at 0 its first stage reuse gives up at once, the kernel drains its
-    MMAs and frees its tensor memory, and the call returns CDG_ETIMEOUT; with
-    the limit restored the same handle applies within 1e-13."""
+    limit at 0 the first wait of each role (the issuing thread's wait for a
+    stage's copies, the epilogue's wait for a finished row) gives up at once,
+    the kernel drains its copies and MMAs and frees its tensor memory, and the
+    call returns CDG_ETIMEOUT; with the limit restored the same handle applies
+    within 1e-13."""
     import torch
     from paper_2012_08024_gb300 import CdgError, Solver
     S = Solver(jittered_square(10), p=3, max_levels=3, precision="fp32", nrhs=128, tc_fp64_apply=True).bind()
