@@ -243,6 +243,8 @@ def run_extras(pkg, dev, stream, barrier, only=None):
         out.update(extra_multi_rhs(pkg, dev, stream))
     if only == "tc_small":
         out.update(extra_tc_small(pkg, dev, stream))
+    if only == "mr_small":
+        out.update(extra_mr_small(pkg, dev, stream))
     if only in ("multi_rhs_bf16", "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply"):
         out.update(extra_multi_rhs(pkg, dev, stream, variants=(only[10:],), singles=False))   # one variant
     if only in (None, "adjoint"):
@@ -317,6 +319,32 @@ def extra_tc_small(pkg, dev, stream):
     S.solve_multi(fq)
     torch.cuda.synchronize(dev)
     return {"tc_small": {"split_fp64_apply_ms": ms, "dofs": int(mesh.n_elements * 10), "nrhs": R}}
+
+
+def extra_mr_small(pkg, dev, stream):
+    """A small case of the many-right-hand-side V-cycle sweeps (the size ncu
+    captures in full): 100 x 100 square (20,000 triangles, p = 3, 200,000
+    dofs), 256 right-hand sides (one FP32 V-cycle vector: 205 MB, above L2),
+    two CG iterations with FP32 blocks (CUDA-core sweeps, autotuned), then two
+    with BF16 blocks and tcgen05 sweeps.  Each solve runs inside an NVTX range
+    ("mr_fp32", "mr_bf16_tc") so that a profiler can pick its kernels out."""
+    import torch
+    from synthetic import jittered_square, sine_combination_sources
+    mesh = jittered_square(100)
+    R = 256
+    out = {}
+    for prec, tc, tag in (("fp32", False, "mr_fp32"), ("bf16", True, "mr_bf16_tc")):
+        S = pkg.Solver(mesh, p=3, max_levels=4, nu_pre=2, nu_post=2, precision=prec, nrhs=R, maxit=2,
+                       tensor_cores=tc).bind(dev)
+        fq = torch.tensor(sine_combination_sources(S.quadrature_points()[0], R, mmax=8, seed0=0), device=dev)
+        S.solve_multi(fq)   # the autotuner's timings run here, outside the range
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_push(tag)
+        ms, _ = _time(lambda: S.solve_multi(fq), stream, 1)
+        torch.cuda.nvtx.range_pop()
+        out[tag + "_two_iterations_ms"] = ms
+        del S
+    return {"mr_small": out}
 
 
 def extra_batched(pkg, dev, stream):
@@ -487,7 +515,7 @@ def main():
                          "kernels; the form a kernel profiler lists launch by launch)")
     ap.add_argument("--only-extra", default=None,
                     choices=["latency", "batched", "multi_rhs", "adjoint", "tet48", "multi_rhs_bf16",
-                             "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply", "tc_small"],
+                             "multi_rhs_bf16_cuda_cores", "multi_rhs_fp32_tc_fp64_apply", "tc_small", "mr_small"],
                     help="run one extra workload alone and print its numbers (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

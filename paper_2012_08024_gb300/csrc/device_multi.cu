@@ -360,14 +360,21 @@ __global__ void mr_update_kernel(int nrows, int R, int G, const double* __restri
   partial[(size_t)g * R + r] = s;
 }
 
-// p = z + beta_r p per column (p = z on the first step); z is the V-cycle's FP32 output
+// p = z + beta_r p per column (p = z on the first step); z is the V-cycle's FP32 output.
+// With maxb, also the largest biased FP64 exponent of each column of the new p
+// (atomicMax over the CTAs; maxb zeroed before), which the split apply needs
+__device__ __forceinline__ int biased_exp(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
 __global__ void mr_p_kernel(int nrows, int R, int G, const double* __restrict__ scal, int first,
-                            const float* __restrict__ z, double* __restrict__ p) {
+                            const float* __restrict__ z, double* __restrict__ p, int* __restrict__ maxb) {
   const int g = blockIdx.x, r = threadIdx.x;
   if (r >= R) return;
   int lo, hi;
   mr_rows(nrows, G, g, lo, hi);
   const double beta = first ? 0.0 : scal[(size_t)r * S_COUNT + S_BETA];
+  int em = 0;
   int row = lo;
   for (; row + 4 <= hi; row += 4) {
     float zv[4];   // raw words first, conversions after (see mr_dot_kernel)
@@ -381,14 +388,19 @@ __global__ void mr_p_kernel(int nrows, int R, int G, const double* __restrict__ 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const double zo = f32_to_f64(zv[u]);
-      p[(size_t)(row + u) * R + r] = first ? zo : fma(beta, pv[u], zo);
+      const double v = first ? zo : fma(beta, pv[u], zo);
+      p[(size_t)(row + u) * R + r] = v;
+      em = max(em, biased_exp(v));
     }
   }
   for (; row < hi; ++row) {
     const size_t o = (size_t)row * R + r;
     const double zo = f32_to_f64(z[o]);
-    p[o] = first ? zo : fma(beta, p[o], zo);
+    const double v = first ? zo : fma(beta, p[o], zo);
+    p[o] = v;
+    em = max(em, biased_exp(v));
   }
+  if (maxb) atomicMax(maxb + r, em);
 }
 
 // b[k][i][r] = sum_q w_q phi_i(x_q) f[r][K][q], K = perm0[k]  (f only; zero boundary data)
@@ -731,11 +743,15 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
   return true;
 }
 
-bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t s) {
+// maxb_ready: the column exponents of x are already in M.oz_maxb (mr_p_kernel
+// stores them for p); pq_groups (split apply only): the apply also leaves the
+// partial sums of x . y in M.partial, *pq_groups of them per column
+bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t s, bool maxb_ready = false,
+                int* pq_groups = nullptr) {
   const DevLevel& L0 = D.lev[0];
   if (M.oz)
-    return oz_apply(D.np, L0.n, M.R, L0.rowptr, L0.col, M.oz_img, M.oz_eA, M.oz_xs, M.oz_maxb, x, y, M.tc_err,
-                    D.wait_limit, s);
+    return oz_apply(D.np, L0.n, M.R, L0.rowptr, L0.col, M.oz_img, M.oz_eA, M.oz_xs, M.oz_maxb, maxb_ready, x, y,
+                    pq_groups ? M.partial : nullptr, pq_groups, M.tc_err, D.wait_limit, s);
   const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0), rc = cols_of(M, 0, 0);
   MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, L0.n, M.R, L0.rowptr, L0.col, L0.A,
                                                                      x, (const double*)nullptr, y, 0.0, s)));
@@ -807,8 +823,10 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
   return ok;
 }
 
-void mr_finalize(MR& M, int which, bool flexible, double tol, cudaStream_t s) {
-  mr_finalize_kernel<<<(M.R + 127) / 128, 128, 0, s>>>(M.R, M.G, M.partial, which, flexible ? 1 : 0, tol, M.scal);
+// sums G partials per column (G = M.G unless given) into the CG scalars
+void mr_finalize(MR& M, int which, bool flexible, double tol, cudaStream_t s, int G = 0) {
+  mr_finalize_kernel<<<(M.R + 127) / 128, 128, 0, s>>>(M.R, G > 0 ? G : M.G, M.partial, which, flexible ? 1 : 0, tol,
+                                                         M.scal);
   count_launch();
 }
 
@@ -894,15 +912,22 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
     count_launch();
     ok = precond();
     mr_dot<float>(D, M, M.r, M.z32, nullptr, 2, o.tol, s);
-    mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 1, M.z32, M.p);
+    if (M.oz) cudaMemsetAsync(M.oz_maxb, 0, sizeof(int) * R, s);
+    mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 1, M.z32, M.p, M.oz ? M.oz_maxb : nullptr);
     count_launch();
     while (ok) {
       if (it >= o.maxit) {
         status = CDG_ENOCONV;
         break;
       }
-      ok = mr_apply64(D, M, M.p, M.q, s);
-      mr_dot<double>(D, M, M.p, M.q, nullptr, 0, o.tol, s);
+      if (M.oz) {   // p's column exponents come from mr_p_kernel, p . A p from the apply's epilogue
+        int gq = 0;
+        ok = mr_apply64(D, M, M.p, M.q, s, true, &gq);
+        mr_finalize(M, 0, false, o.tol, s, gq);
+      } else {
+        ok = mr_apply64(D, M, M.p, M.q, s);
+        mr_dot<double>(D, M, M.p, M.q, nullptr, 0, o.tol, s);
+      }
       mr_update_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, M.p, M.q, M.x, M.r, M.r32, M.partial);
       count_launch();
       mr_finalize(M, 1, false, o.tol, s);
@@ -934,7 +959,8 @@ int dev_solve_multi(cdg_handle* h, const double* f_q, double* u, double* res_his
       std::swap(M.z32, M.z32old);
       ok = precond();
       mr_dot<float>(D, M, M.r, M.z32, M.z32old, 2, o.tol, s);
-      mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 0, M.z32, M.p);
+      if (M.oz) cudaMemsetAsync(M.oz_maxb, 0, sizeof(int) * R, s);
+      mr_p_kernel<<<M.G, T, 0, s>>>((int)nrows, R, M.G, M.scal, 0, M.z32, M.p, M.oz ? M.oz_maxb : nullptr);
       count_launch();
     }
   }

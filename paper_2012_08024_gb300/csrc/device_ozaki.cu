@@ -201,7 +201,10 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 
-// CTA (x, c) owns the block rows K = x, x + gridDim.x, ... and column tile c,
+// CTA (x, c) owns the block rows K = x, x + gridDim.x, ... and column tile c
+// (strided, so that the CTAs working at the same time cover neighbouring rows
+// and share the X images of their neighbours in L2; contiguous row ranges per
+// CTA measured a 25% instead of 46% L2 hit rate and 1.8x the DRAM reads),
 // with two roles that run concurrently:
 //  - lane 0 of warp 4 streams the blocks of those rows through a ring of
 //    kStages shared-memory stages (a stage is free once the MMAs that read it
@@ -211,7 +214,9 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 //    acce[a], until the epilogue has read that set's previous row.
 //  - warps 0-3 (lane = column of the tile) wait on accf[a], read the row's S
 //    accumulators, release the set (acce[a], one arrive per warp), combine
-//    them exactly and write y.
+//    them exactly and write y.  With pq_partial they also sum x . y over the
+//    CTA's rows, in row order, into pq_partial[blockIdx.x][column] (the CG's
+//    p . A p, without a separate pass over both vectors).
 // So the MMAs of row k + 1 run while the epilogue of row k converts and
 // stores.  Every wait is bounded; a role that gives up sets the shared fail
 // flag, on which the other role's waits give up too.  Before the CTA ends the
@@ -225,7 +230,9 @@ __global__ void __launch_bounds__(kOzThreads, 2) oz_apply_kernel(int n, int R, i
                                                                const int* __restrict__ eA,
                                                                const unsigned char* __restrict__ xs,
                                                                const int* __restrict__ maxb, double* __restrict__ y,
-                                                               int* __restrict__ err, int wait_limit) {
+                                                               const double* __restrict__ xdot,
+                                                               double* __restrict__ pq_partial, int* __restrict__ err,
+                                                               int wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAccSets], acce[kAccSets], fin;
   __shared__ uint32_t tmem_base;
@@ -337,6 +344,8 @@ __global__ void __launch_bounds__(kOzThreads, 2) oz_apply_kernel(int n, int R, i
     const int r = c * kTile + tid;   // this thread's column
     const int ex = r < R ? maxb[r] - 1022 : 0;
     const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    const bool dot = pq_partial != nullptr && r < R;
+    double dsum = 0.0;   // with pq_partial: sum over this CTA's rows of x . y for column r
     int rowi = 0;
     for (int K = blockIdx.x; K < n; K += gridDim.x) {
       const int b0 = rowptr[K], b1 = rowptr[K + 1];
@@ -346,6 +355,13 @@ __global__ void __launch_bounds__(kOzThreads, 2) oz_apply_kernel(int n, int R, i
         continue;
       }
       const int a = rowi % kAccSets;
+      int kexp[NP];   // the row's scale exponents (and x, for the dot), loaded before the wait
+      double xd[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        kexp[i] = eA[(size_t)K * 16 + i] + ex - 63;
+        xd[i] = dot ? xdot[((size_t)K * NP + i) * R + r] : 0.0;
+      }
       const bool got = wait_or_fail(smem_u32(&accf[a]), (uint32_t)((rowi / kAccSets) & 1), wait_limit, &fail_s);
       if (!__all_sync(0xffffffffu, got ? 1 : 0)) {   // the warp leaves together (tcgen05.ld is warp-wide)
         if (lane == 0) {
@@ -387,12 +403,14 @@ __global__ void __launch_bounds__(kOzThreads, 2) oz_apply_kernel(int n, int R, i
       if (r < R) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          const int k = eA[(size_t)K * 16 + i] + ex - 63;
-          y[((size_t)K * NP + i) * R + r] = i64_scaled(vh[i], k + 28) + i64_scaled(vl[i], k);
+          const double v = i64_scaled(vh[i], kexp[i] + 28) + i64_scaled(vl[i], kexp[i]);
+          y[((size_t)K * NP + i) * R + r] = v;
+          if (dot) dsum = fma(xd[i], v, dsum);
         }
       }
       ++rowi;
     }
+    if (dot) pq_partial[(size_t)blockIdx.x * R + r] = dsum;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -463,11 +481,15 @@ bool oz_prepare(const cdg::BSR& A, int np, std::vector<uint16_t>& img, std::vect
 
 // y = A_0 x for R columns ([n][np][R] FP64 vectors): column exponents, slices of x, tensor-core products.
 bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const void* img, const int* eA, void* xs,
-              int* maxb, const double* x, double* y, int* err, int wait_limit, cudaStream_t s) {
+              int* maxb, bool maxb_ready, const double* x, double* y, double* pq_partial, int* pq_groups, int* err,
+              int wait_limit, cudaStream_t s) {
   const size_t nrows = (size_t)n * np;
-  cudaMemsetAsync(maxb, 0, sizeof(int) * R, s);
-  const unsigned ty = (unsigned)((R + 255) / 256);
-  oz_colexp_kernel<<<dim3(2 * 152, ty), 256, 0, s>>>(nrows, R, x, maxb);
+  if (!maxb_ready) {
+    cudaMemsetAsync(maxb, 0, sizeof(int) * R, s);
+    const unsigned ty = (unsigned)((R + 255) / 256);
+    oz_colexp_kernel<<<dim3(2 * 152, ty), 256, 0, s>>>(nrows, R, x, maxb);
+    count_launch();
+  }
   const int tiles = (R + kTile - 1) / kTile;
   const int lim = wait_limit < 0 ? kWaitLimit : std::min(wait_limit, kWaitLimit);
   // two CTAs per SM (108 KB of shared memory, 256 TMEM columns each): the whole grid is resident
@@ -477,7 +499,7 @@ bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const voi
     slice<<<4 * 152 * 4, 256, 0, s>>>(n, R, tiles, x, maxb, (unsigned char*)xs);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     kern<<<grid, kOzThreads, smem, s>>>(n, R, tiles, rowptr, col, (const unsigned char*)img, eA,
-                                   (const unsigned char*)xs, maxb, y, err, lim);
+                                        (const unsigned char*)xs, maxb, y, x, pq_partial, err, lim);
   };
   switch (np) {
     case 3: go(oz_slice_kernel<3>, oz_apply_kernel<3>); break;
@@ -486,6 +508,7 @@ bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const voi
     case 10: go(oz_slice_kernel<10>, oz_apply_kernel<10>); break;
     default: return false;
   }
-  count_launch(3);
+  count_launch(2);
+  if (pq_groups) *pq_groups = (int)grid.x;
   return true;
 }

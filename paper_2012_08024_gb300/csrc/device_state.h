@@ -199,8 +199,13 @@ size_t oz_image_bytes(const cdg::BSR& A);
 size_t oz_xslice_bytes(int64_t n, int np, int R);
 bool oz_feasible(const cdg::BSR& A, int np);
 bool oz_prepare(const cdg::BSR& A, int np, std::vector<uint16_t>& img, std::vector<int32_t>& eA);
+// y = A_0 x by exact splitting; maxb [R] receives the largest biased FP64
+// exponent of every column of x, unless maxb_ready says the caller already
+// stored it there (the CG's p update does).  pq_partial (nullable): per-CTA
+// partial sums of x . y per column, [*pq_groups][R], for the CG's p . A p.
 bool oz_apply(int np, int n, int R, const int* rowptr, const int* col, const void* img, const int* eA, void* xs,
-              int* maxb, const double* x, double* y, int* err, int wait_limit, cudaStream_t s);
+              int* maxb, bool maxb_ready, const double* x, double* y, double* pq_partial, int* pq_groups, int* err,
+              int wait_limit, cudaStream_t s);
 void mr_tuning(const MR& M, int level, int nlev, int32_t* out);
 
 // device_tc.cu: multi-right-hand-side smoother sweep y = x + omega (bh - x - Ahat x) on
