@@ -57,9 +57,9 @@ __device__ __forceinline__ void stage_block(TC* s, const TA* a, int ne) {
 constexpr int kMrMaxBR = 4;
 
 template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
-__global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
-                              const TA* __restrict__ A, const TV* __restrict__ x, const TV* __restrict__ b,
-                              TV* __restrict__ y, TC omega) {
+__device__ __forceinline__ void mr_bsr_body(int n, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                            const TA* __restrict__ A, const TV* __restrict__ x,
+                                            const TV* __restrict__ b, TV* __restrict__ y, TC omega) {
   __shared__ __align__(16) TC as[kMrMaxBR][NP * NP];
   const int BR = (int)blockDim.y, TX = (int)blockDim.x;
   const int K0 = blockIdx.x * BR;
@@ -118,6 +118,24 @@ __global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, cons
       else y[o] = (TV)((TC)x[o] + omega * ((TC)b[o] - (TC)x[o] - acc[c][i]));
     }
   }
+}
+
+template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
+__global__ void mr_bsr_kernel(int n, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const TA* __restrict__ A, const TV* __restrict__ x, const TV* __restrict__ b,
+                              TV* __restrict__ y, TC omega) {
+  mr_bsr_body<TA, TV, TC, NP, MODE, C>(n, R, rowptr, col, A, x, b, y, omega);
+}
+
+// The same for CTAs of at most 128 threads, with the registers held so that
+// eight such CTAs fit on an SM: the V-cycle sweeps wait on their x gathers,
+// and more resident warps hide more of that latency (an autotuner choice).
+template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
+__global__ void __launch_bounds__(128, 8) mr_bsr_kernel_lb(int n, int R, const int* __restrict__ rowptr,
+                                                         const int* __restrict__ col, const TA* __restrict__ A,
+                                                         const TV* __restrict__ x, const TV* __restrict__ b,
+                                                         TV* __restrict__ y, TC omega) {
+  mr_bsr_body<TA, TV, TC, NP, MODE, C>(n, R, rowptr, col, A, x, b, y, omega);
 }
 
 // per element K: out = B_K in (block-diagonal apply); with WRITE_X also x = omega out
@@ -458,6 +476,7 @@ struct MR {
   int tile[kMaxLev][4] = {};
   int rows[kMaxLev][4] = {};
   int cols[kMaxLev][4] = {};   // right-hand sides per thread
+  int lb[kMaxLev][4] = {};     // 1: the register-capped instance (CTAs of at most 128 threads)
   bool tuned = false;
   bool tc = false;             // smoother sweeps on tcgen05 (BF16 blocks)
   int* tc_err = nullptr;       // set by a tensor-core kernel whose wait timed out
@@ -628,8 +647,18 @@ int max_threads_of(Kern k) {
 }
 
 template <typename TA, typename TV, typename TC, int NP, int MODE, int C>
-void mr_bsr_launch_c(int tx, int br, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
+void mr_bsr_launch_c(int tx, int br, bool lb, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
                      const TV* b, TV* y, TC omega, cudaStream_t s) {
+  if constexpr (C <= 2 && sizeof(TC) == 4) {   // the register-capped instance: FP32 arithmetic, <= 2 columns
+    if (lb && tx * std::min(std::max(br, 1), kMrMaxBR) <= 128) {
+      br = std::min(std::max(br, 1), kMrMaxBR);
+      const dim3 grid((unsigned)((n + br - 1) / br), (unsigned)((R + tx * C - 1) / (tx * C))),
+          block((unsigned)tx, (unsigned)br);
+      mr_bsr_kernel_lb<TA, TV, TC, NP, MODE, C><<<grid, block, 0, s>>>(n, R, rp, cl, A, x, b, y, omega);
+      count_launch();
+      return;
+    }
+  }
   static const int mt = max_threads_of(mr_bsr_kernel<TA, TV, TC, NP, MODE, C>);
   br = std::min(std::max(br, 1), kMrMaxBR);
   // a CTA larger than the register file allows runs as fewer block rows, then
@@ -645,16 +674,17 @@ void mr_bsr_launch_c(int tx, int br, int n, int R, const int* rp, const int* cl,
 // mr_bsr_kernel with tx threads across the right-hand sides, rc columns per
 // thread (a tile of tx rc columns) and br block rows per CTA
 template <typename TA, typename TV, typename TC, int NP, int MODE>
-void mr_bsr_launch(int tx, int br, int rc, int n, int R, const int* rp, const int* cl, const TA* A, const TV* x,
-                   const TV* b, TV* y, TC omega, cudaStream_t s) {
-  if (rc >= 4) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 4>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
-  else if (rc == 2) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 2>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
-  else mr_bsr_launch_c<TA, TV, TC, NP, MODE, 1>(tx, br, n, R, rp, cl, A, x, b, y, omega, s);
+void mr_bsr_launch(int tx, int br, int rc, bool lb, int n, int R, const int* rp, const int* cl, const TA* A,
+                   const TV* x, const TV* b, TV* y, TC omega, cudaStream_t s) {
+  if (rc >= 4) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 4>(tx, br, lb, n, R, rp, cl, A, x, b, y, omega, s);
+  else if (rc == 2) mr_bsr_launch_c<TA, TV, TC, NP, MODE, 2>(tx, br, lb, n, R, rp, cl, A, x, b, y, omega, s);
+  else mr_bsr_launch_c<TA, TV, TC, NP, MODE, 1>(tx, br, lb, n, R, rp, cl, A, x, b, y, omega, s);
 }
 
 inline int tile_of(const MR& M, int l, int mode) { return M.tile[l][mode] ? M.tile[l][mode] : (int)threads_for(M.R); }
 inline int rows_of(const MR& M, int l, int mode) { return M.rows[l][mode] ? M.rows[l][mode] : 1; }
 inline int cols_of(const MR& M, int l, int mode) { return M.cols[l][mode] ? M.cols[l][mode] : 1; }
+inline bool lb_of(const MR& M, int l, int mode) { return M.lb[l][mode] != 0; }
 
 template <typename TA>
 bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, float* z0, cudaStream_t s) {
@@ -667,11 +697,12 @@ bool mr_vcycle(DeviceState& D, MR& M, const cdg_options& o, const float* b0, flo
     if (mode == 3 && M.tc)
       return mr_tc_smooth(np, n, R, rp, cl, A, x, b, y, w, M.tc_err, D.wait_limit, s);
     const int tx = tile_of(M, l, mode), br = rows_of(M, l, mode), rc = cols_of(M, l, mode);
+    const bool lb = lb_of(M, l, mode);
     MR_NP_DISPATCH(np, {
       if (mode == 1)
-        mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, n, R, rp, cl, (const float*)A, x, b, y, w, s);
+        mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, lb, n, R, rp, cl, (const float*)A, x, b, y, w, s);
       else
-        mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, n, R, rp, cl, (const TA*)A, x, b, y, w, s);
+        mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, lb, n, R, rp, cl, (const TA*)A, x, b, y, w, s);
     });
     return true;
   };
@@ -753,7 +784,8 @@ bool mr_apply64(DeviceState& D, MR& M, const double* x, double* y, cudaStream_t 
     return oz_apply(D.np, L0.n, M.R, L0.rowptr, L0.col, M.oz_img, M.oz_eA, M.oz_xs, M.oz_maxb, maxb_ready, x, y,
                     pq_groups ? M.partial : nullptr, pq_groups, M.tc_err, D.wait_limit, s);
   const int tx = tile_of(M, 0, 0), br = rows_of(M, 0, 0), rc = cols_of(M, 0, 0);
-  MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, L0.n, M.R, L0.rowptr, L0.col, L0.A,
+  MR_NP_DISPATCH(D.np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, false, L0.n, M.R, L0.rowptr, L0.col,
+                                                                     L0.A,
                                                                      x, (const double*)nullptr, y, 0.0, s)));
   return true;
 }
@@ -777,12 +809,17 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
         if (rc > 1 && tx * rc > tmax) break;   // a thread's extra columns would all be padding
         for (int br : {1, 2, 4}) {
           if (tx * br > 1024) continue;
-          const float t = time_calls(s, e0, e1, 2, [&] { launch_one(tx, br, rc); });
-          if (t < tbest) {
-            tbest = t;
-            M.tile[l][mode] = tx;
-            M.rows[l][mode] = br;
-            M.cols[l][mode] = rc;
+          // the register-capped instance exists for FP32 arithmetic, CTAs of <= 128 threads, rc <= 2
+          const bool lb_ok = mode != 0 && rc <= 2 && tx * br <= 128;
+          for (int lb = 0; lb <= (lb_ok ? 1 : 0); ++lb) {
+            const float t = time_calls(s, e0, e1, 2, [&] { launch_one(tx, br, rc, lb != 0); });
+            if (t < tbest) {
+              tbest = t;
+              M.tile[l][mode] = tx;
+              M.rows[l][mode] = br;
+              M.cols[l][mode] = rc;
+              M.lb[l][mode] = lb;
+            }
           }
         }
       }
@@ -793,8 +830,9 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
     const DevLevel& L0 = D.lev[0];
     const size_t nv = (size_t)L0.n * np * R;
     cudaMemsetAsync(M.p, 0, nv * sizeof(double), s);
-    pick(0, 0, [&](int tx, int br, int rc) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, L0.n, R, L0.rowptr, L0.col, L0.A,
+    pick(0, 0, [&](int tx, int br, int rc, bool) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<double, double, double, NP, 0>(tx, br, rc, false, L0.n, R, L0.rowptr, L0.col,
+                                                                         L0.A,
                                                                          (const double*)M.p, (const double*)nullptr,
                                                                          M.q, 0.0, s)));
     });
@@ -805,13 +843,13 @@ bool mr_autotune(DeviceState& D, MR& M, double omega, cudaStream_t s) {
     MRLevel& L = M.lev[l];
     const size_t nv = (size_t)DL.n * np * R;
     for (float* v : {L.x, L.b, L.bh, L.t}) cudaMemsetAsync(v, 0, nv * sizeof(float), s);
-    pick(l, 1, [&](int tx, int br, int rc) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, DL.n, R, DL.rowptr, DL.col,
+    pick(l, 1, [&](int tx, int br, int rc, bool lb) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<float, float, float, NP, 1>(tx, br, rc, lb, DL.n, R, DL.rowptr, DL.col,
                                                                       (const float*)L.A, (const float*)L.x,
                                                                       (const float*)L.b, L.t, w, s)));
     });
-    pick(l, 3, [&](int tx, int br, int rc) {
-      MR_NP_DISPATCH_V(np, (mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, DL.n, R, DL.hrowptr, DL.hcol,
+    pick(l, 3, [&](int tx, int br, int rc, bool lb) {
+      MR_NP_DISPATCH_V(np, (mr_bsr_launch<TA, float, float, NP, 3>(tx, br, rc, lb, DL.n, R, DL.hrowptr, DL.hcol,
                                                                    (const TA*)L.Ahat, (const float*)L.x,
                                                                    (const float*)L.bh, L.t, w, s)));
     });
