@@ -1,13 +1,17 @@
 // Many right-hand sides on one mesh (cdg_solve_multi): the same V-cycle
 // preconditioned CG run for R columns at once.  Vectors are [n_l][n_p][R]
 // (the R columns of one element's coefficient i are contiguous), so one block
-// of an operator is read once per R columns: a CTA owns one block row and its
-// R threads own one column each; the block is staged in shared memory and
-// every thread applies it to its column.  The outer CG (residual, dots, updates,
-// the level-0 operator) is FP64 with per-column scalars; the V-cycle runs on
-// FP32 arithmetic on FP32 copies of the level operators, or (precision 2) on
-// BF16 copies of the row-scaled smoother blocks D^-1(A - D) and of the transfer
-// blocks (the residual operator and the block inverses stay FP32).
+// of an operator is read once per tile of columns: a CTA owns one to four
+// block rows and a tile of columns, stages the rows' blocks in shared memory,
+// and each thread applies them to one, two or four columns of the tile (the
+// autotuner picks the shape).  The outer CG (residual, dots, updates, the
+// level-0 operator) is FP64 with per-column scalars, its vector passes fused
+// (the update also writes the FP32 copy of r for the V-cycle and the partial
+// sums of r.r); the V-cycle runs on FP32 arithmetic on FP32 copies of the
+// level operators, or (precision 2) on BF16 copies of the row-scaled smoother
+// blocks D^-1(A - D) and of the transfer blocks (the residual operator and the
+// block inverses stay FP32).  The level-0 operator can also run on the tensor
+// cores by exact splitting (device_ozaki.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
